@@ -1,0 +1,357 @@
+"""Benchmark: solved systems/s for very many small nonlinear systems on one GB300.
+
+Workload (default): 2^20 independent instances of the dense cubic family
+F(u) = A u + u.*u.*u - b with n = 8, A = 3 I + G (G ~ N(0, 0.3^2)),
+b ~ U[-5, 5]^8, u0 = 0, abstol 1e-10, maxiters 50, seed 0.  One step solves
+the whole batch four times: Newton with backtracking and trust-region
+dogleg, each in FP64 and in mixed precision (FP32 Jacobian and LU, FP64
+residual / norm / merit / update).  A system counts as solved when its
+status is SUCCESS, i.e. its FP64 residual satisfies ||F||_inf <= 1e-10.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on the
+host cores over a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2403_16341_gb300 import inputs as I  # noqa: E402
+
+N_SYS = 8
+B_FULL = 1 << 20
+ABSTOL = 1e-10
+MAXITERS = 50
+NEWTON, LS, TR = 0, 1, 2
+MIXED = 1 << 8
+VARIANTS = [("newton_backtrack_fp64", LS), ("newton_backtrack_mixed", LS | MIXED),
+            ("trust_dogleg_fp64", TR), ("trust_dogleg_mixed", TR | MIXED)]
+WORKLOAD = "cubic n=8, 2^20 instances, NR+backtracking and TR-dogleg x {FP64, mixed}"
+METRIC = "solved systems/s at ||F||inf<=1e-10 (FP64 vs mixed, 1 GB300)"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x DFMA/clk x flop/FMA x max clock
+
+
+def algorithmic_fp64_flops(n: int, alg: int, iters: np.ndarray, nfev: np.ndarray) -> float:
+    """Useful FP64 flops of one solve batch (dual-number and padding overheads
+    are implementation cost and not counted).  Per residual evaluation of the
+    cubic: 2n^2 + 3n, plus 2n for the squared norm and 2n for forming the
+    trial point.  In FP64 mode every pass also factors and solves:
+    LU 2n^3/3 - n^2/2 - n/6, triangular solves 2n^2, analytic-equivalent
+    Jacobian 2n, J^T F 2n^2 (line search) or J^T F and J g 4n^2 plus 10n for
+    the dogleg (trust region).  Mixed mode runs the Jacobian and the LU in
+    FP32, so only the residual-side terms are FP64."""
+    res = (2 * n * n + 3 * n) + 2 * n + 2 * n
+    f = float(nfev.sum()) * res
+    if not alg & MIXED:
+        per_pass = (2 * n ** 3 / 3 - n * n / 2 - n / 6) + 2 * n * n + 2 * n
+        per_pass += 2 * n * n if (alg & 0xFF) == LS else 4 * n * n + 10 * n
+        f += float(iters.sum()) * per_pass
+    return f
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows: list[list[str]] = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self) -> dict:
+        sm = [float(r[0]) for r in self.rows if len(r) >= 7 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 7 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 7 for i in range(4)
+                          if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_rate(batch, threads: int, sample: int):
+    """FP64 oracle over the first `sample` instances, both algorithms."""
+    import oracle as O
+    sub = I.Batch(batch.family, batch.n, np.ascontiguousarray(batch.params[:, :sample]),
+                  np.ascontiguousarray(batch.u0[:, :sample]))
+    solved, t0 = 0, time.perf_counter()
+    for oalg in (O.ALG_NEWTON_BACKTRACK, O.ALG_TRUST_DOGLEG):
+        _, st, *_ = O.solve_batch(sub.family, sub.params, sub.u0, oalg, ABSTOL, MAXITERS,
+                                  threads=threads)
+        solved += int((st == 0).sum())
+    dt = time.perf_counter() - t0
+    return solved / dt, dt, solved
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    B = min(B_FULL, args.sample)
+    batch = I.workload_cubic_n8(B)
+    for _ in range(args.warmup):
+        oracle_rate(batch, threads, min(B, 4096))
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, dt, _ = oracle_rate(batch, threads, B)
+        rates.append(r)
+        times.append(dt)
+    value = float(np.median(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solved systems/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.median(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_instances": B, "algorithms": ["LS", "TR"]},
+            "cpu_baseline": {"value": value, "unit": "solved systems/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": f"first {B} of the 2^20 instances, NR+backtracking and "
+                                       "TR-dogleg in FP64 (the oracle has no mixed mode)"},
+            "e2e": {"value": value, "unit": "solved systems/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2403_16341_gb300 as nls
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    solver = nls.Solver(local, stream)
+
+    # every rank solves its own 2^20 instances (weak scaling, no exchange)
+    batch = I.cubic_batch(N_SYS, B_FULL, seed=rank, config_id=1, b_half_width=5.0)
+    params = torch.from_numpy(batch.params).to(dev)
+    u0 = torch.from_numpy(batch.u0).to(dev)
+    us = [torch.empty_like(u0) for _ in VARIANTS]
+    B = batch.batch
+    outs = [tuple(torch.empty(B, dtype=dt, device=dev) for dt in
+                  (torch.int32, torch.int32, torch.float64, torch.int32)) for _ in VARIANTS]
+    def new_events():
+        return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in VARIANTS]
+
+    def step(events=None):
+        reqs = []
+        for i, (_, alg) in enumerate(VARIANTS):
+            us[i].copy_(u0)
+            if events:
+                events[i][0].record(stream)
+            reqs.append(solver.submit(batch.family, params, us[i], alg, ABSTOL, MAXITERS, outs[i]))
+            solver.flush()
+            if events:
+                events[i][1].record(stream)
+        return reqs
+
+    def finish(reqs):
+        return [solver.wait(r) for r in reqs]
+
+    for _ in range(max(args.warmup, 3)):
+        finish(step())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    l0 = solver.launches()
+    per_variant = [[] for _ in VARIANTS]
+    solved_total = 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        all_reqs, all_events = [], []
+        for _ in range(args.steps):
+            ev = new_events()
+            all_reqs.append(step(ev))
+            all_events.append(ev)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        for reqs, ev in zip(all_reqs, all_events):
+            solved_total += sum(finish(reqs))
+            for i in range(len(VARIANTS)):
+                per_variant[i].append(ev[i][0].elapsed_time(ev[i][1]))
+    launches = solver.launches() - l0
+    ms_total = t0.elapsed_time(t1)
+    if dist:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        s = torch.tensor([solved_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(s)
+        solved_total = int(s.item())
+    ms_step = ms_total / args.steps
+    value = solved_total / (ms_total / 1e3)
+
+    # per-variant numbers and the roofline of the dominant kernel
+    variants = {}
+    dom, dom_ms = None, -1.0
+    for i, (name, alg) in enumerate(VARIANTS):
+        st, it, rs, nf = (t.cpu().numpy() for t in outs[i])
+        ms = float(np.median(per_variant[i]))
+        fl = algorithmic_fp64_flops(N_SYS, alg, it, nf)
+        solved = int((st == 0).sum())
+        variants[name] = {"ms": ms, "solved_per_s": solved / (ms / 1e3), "solved": solved,
+                          "mean_iters": float(it.mean()), "max_iters": int(it.max()),
+                          "fp64_gflop": fl / 1e9, "fp64_tflops": fl / (ms / 1e3) / 1e12,
+                          "max_resid": float(rs.max())}
+        if ms > dom_ms:
+            dom, dom_ms = name, ms
+    dv = variants[dom]
+
+    # the comparison bar: plain FP64 Newton, one static thread per instance
+    solver.set_option(nls.NLS_OPT_PERSISTENT, 0)
+    ub = torch.empty_like(u0)
+    bo = tuple(torch.empty(B, dtype=dt, device=dev) for dt in
+               (torch.int32, torch.int32, torch.float64, torch.int32))
+    bt = []
+    for r in range(4):
+        ub.copy_(u0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        req = solver.submit(batch.family, params, ub, NEWTON, ABSTOL, MAXITERS, bo)
+        solver.flush()
+        e1.record(stream)
+        sb = solver.wait(req)
+        torch.cuda.synchronize()
+        if r:
+            bt.append(e0.elapsed_time(e1))
+    solver.set_option(nls.NLS_OPT_PERSISTENT, 1)
+    baseline = {"kernel": "plain FP64 Newton, one thread per instance, static grid",
+                "ms": float(np.median(bt)), "solved_per_s": sb / (float(np.median(bt)) / 1e3)}
+
+    # end to end through the C ABI on pinned host buffers
+    hp = torch.from_numpy(batch.params).pin_memory()
+    hu0 = torch.from_numpy(batch.u0).pin_memory()
+    hu = torch.empty_like(hu0).pin_memory()
+    hst = torch.empty(B, dtype=torch.int32).pin_memory()
+    e2e_times, e2e_solved = [], 0
+    for r in range(2 + args.steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ssum = 0
+        for _, alg in VARIANTS:
+            hu.copy_(hu0)
+            ssum += nls.nls_solve_host(solver.h, batch.family, hp.data_ptr(), hu.data_ptr(), N_SYS,
+                                       B, alg, ABSTOL, MAXITERS, hst.data_ptr(), 0, 0, 0)
+        dt = time.perf_counter() - t
+        if r >= 2:
+            e2e_times.append(dt)
+            e2e_solved += ssum
+    e2e = {"value": e2e_solved / sum(e2e_times), "unit": "solved systems/s",
+           "h2d_bytes_per_step": len(VARIANTS) * (hp.numel() + hu0.numel()) * 8,
+           "d2h_bytes_per_step": len(VARIANTS) * (hu.numel() * 8 + B * 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        sample = min(B, args.sample)
+        rate, dt, _ = oracle_rate(batch, threads, sample)
+        cpu = {"value": rate, "unit": "solved systems/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {sample} of the 2^20 instances, NR+backtracking and TR-dogleg "
+                         f"in FP64 ({dt:.1f} s)"}
+
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    traffic = None
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get(dom)
+        except Exception:
+            traffic = None
+    achieved = dv["fp64_tflops"]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solved systems/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "instances_per_gpu": B, "n": N_SYS,
+                       "abstol": ABSTOL, "maxiters": MAXITERS,
+                       "l2": "inputs larger than L2 (604 MB of parameters per batch)",
+                       "parallelism": f"replicas x{world}"},
+            "variants": variants, "baseline_fp64_newton": baseline,
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                         "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sample", type=int, default=1 << 18,
+                    help="instances the CPU oracle solves per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * nls.h -- C ABI of the GB300 batched small-system nonlinear solver.
+ *
+ * The library solves very many small, independent nonlinear systems
+ *
+ *     find u*_k  such that  F(u*_k; p_k) = 0,   k = 0 .. batch-1,
+ *
+ * (the problem statement of Sec. 2, Eq. 1, with theta = p_k), each instance
+ * with Newton-Raphson (Sec. 2.1, Eq. 2), Newton-Raphson with a backtracking
+ * line search (Sec. 2.2.1, Eq. 8-9) or a trust region with Powell's dogleg
+ * step (Sec. 2.2.2, Eq. 12-14).  The Jacobian comes from forward-mode dual
+ * numbers (Sec. 2.4) or from the family's analytic formula, and each Newton
+ * system is solved with a dense LU with partial pivoting (Sec. 3.2, Fig. 5).
+ * An instance has converged when ||F(u_k)||_inf <= abstol (Sec. 2.1).  The
+ * paper's own GPU form of this path is Sec. 3.4: statically sized,
+ * non-allocating solvers, one instance per GPU thread.
+ *
+ * Conventions for every call:
+ *   - Every function returns an nls_err (0 = NLS_OK, negative = error) and,
+ *     on error, leaves a message for nls_last_error().  Argument errors are
+ *     detected before anything is enqueued.
+ *   - Device pointers are CUDA device (or managed) addresses on the handle's
+ *     device; they stay owned by the caller and must stay valid until the
+ *     request has completed (nls_status returns NLS_OK for it).
+ *   - Per-instance failures (singular Jacobian, NaN, no convergence) are
+ *     never API errors: they are reported per instance as nls_inst_status.
+ *   - A handle is not thread-safe: use one handle per host thread or lock.
+ *
+ * Batch layout ("SoA", element-major, instance fastest): element e of
+ * instance k is at ptr[e * batch + k].  Parameters per family (E values):
+ *   NLS_CUBIC      F = A u + u.*u.*u - b:  e = i*n + j -> A[i][j]
+ *                  (row-major), e = n*n + i -> b[i];          E = n*n + n
+ *   NLS_BRATU      F_i = (u_{i-1} - 2 u_i + u_{i+1}) (n+1)^2 + lambda e^{u_i},
+ *                  u_0 = u_{n+1} = 0 (1-D Bratu, h = 1/(n+1)): e = 0 -> lambda; E = 1
+ *   NLS_SQUARE     F = u.*u - p (the Sec. 2.3 example):  e = i -> p[i];   E = n
+ *   NLS_ROSENBROCK generalized Rosenbrock (Sec. 2.2.1, Eq. 5): no parameters, E = 0
+ */
+#ifndef NLS_H
+#define NLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nls_batch *nls_handle; /* opaque, owned by the library */
+
+enum nls_family { NLS_CUBIC = 0, NLS_BRATU = 1, NLS_SQUARE = 2, NLS_ROSENBROCK = 3 };
+
+/* Algorithm in the low byte of `alg`; flags are OR-ed in. */
+enum nls_alg {
+    NLS_NEWTON = 0,           /* Sec. 2.1, Eq. 2                               */
+    NLS_NEWTON_BACKTRACK = 1, /* Sec. 2.2.1: Armijo (Eq. 8-9), alpha <- alpha/2 */
+    NLS_TRUST_DOGLEG = 2      /* Sec. 2.2.2: Eq. 12-14, Powell's dogleg          */
+};
+#define NLS_ALG_MASK 0xff
+enum nls_flags {
+    NLS_MIXED = 1 << 8,        /* Jacobian + LU in FP32; residual, norm test,
+                                  merit and update in FP64                      */
+    NLS_ANALYTIC_JAC = 1 << 9, /* family's closed-form Jacobian instead of duals */
+    NLS_TILE_THREAD = 1 << 10, /* force one instance per thread   (n <= 8)      */
+    NLS_TILE_WARP = 1 << 11,   /* force one instance per warp     (n <= 32)     */
+    NLS_TILE_CTA = 1 << 12     /* force one instance per CTA      (n <= 128)    */
+};
+
+/* Per-instance outcome. */
+enum nls_inst_status {
+    NLS_SUCCESS = 0,    /* ||F(u)||_inf <= abstol                               */
+    NLS_MAXITERS = 1,   /* maxiters passes without convergence                   */
+    NLS_SINGULAR = 2,   /* an LU pivot was exactly zero or not finite            */
+    NLS_NONFINITE = 3,  /* F became Inf/NaN (at u0, or after a full Newton step) */
+    NLS_LS_FAILED = 4,  /* 30 backtracking trials without sufficient decrease    */
+    NLS_TR_STALLED = 5, /* 32 trust-region rejections in a row                   */
+    NLS_ABORTED = 6     /* not run: the request was cancelled or timed out       */
+};
+
+enum nls_err {
+    NLS_OK = 0,
+    NLS_E_INVALID = -1,     /* bad argument (null pointer, negative size, ...)  */
+    NLS_E_CUDA = -2,        /* a CUDA runtime call failed                       */
+    NLS_E_NOMEM = -3,       /* workspace would exceed the memory cap            */
+    NLS_E_UNSUPPORTED = -4, /* n outside [1, 128], unknown family or tiling     */
+    NLS_E_TIMEOUT = -5,     /* the request did not complete within timeout_ms   */
+    NLS_E_BUSY = -6,        /* the handle is inside another operation           */
+    NLS_E_NOTFOUND = -7     /* unknown request id                               */
+};
+
+/* Fixed algorithm constants (the paper gives no values; see nls_oracle.c
+ * for the same readings):
+ *   backtracking c1 = 1e-4, step factor 1/2, at most 30 trials;
+ *   trust region Delta_0 = 1, accept iff rho > 0, grow x2 (cap 1e3) iff
+ *   rho > 0.75, on rejection shrink x1/4; 32 rejections in a row stall. */
+
+/* Per-instance outputs (all DEVICE pointers, each may be NULL = not written):
+ * status[k] (nls_inst_status), iters[k] (loop passes), resid_inf[k] =
+ * ||F(u_k)||_inf of the returned u_k in FP64, nfev[k] = FP64 residual
+ * evaluations used. */
+typedef struct nls_outputs {
+    int32_t *status;
+    int32_t *iters;
+    double *resid_inf;
+    int32_t *nfev;
+} nls_outputs;
+
+/* Create a solver context on `device` that enqueues on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  mem_cap_bytes bounds
+ * the library-owned device workspace (0 = no cap beyond free memory).
+ * Errors: NLS_E_INVALID (out == NULL), NLS_E_CUDA (bad device). */
+int nls_batch_create(nls_handle *out, int device, void *cuda_stream, size_t mem_cap_bytes);
+
+/* Enqueue the solve of `batch` instances of `family` with size n
+ * (Sec. 2, Eq. 1).  params: DEVICE float64[E * batch] (may be NULL when
+ * E = 0); u: DEVICE float64[n * batch], read as u0 and overwritten with the
+ * returned iterate; out: optional per-instance outputs (NULL = none).
+ * alg = nls_alg | nls_flags.  abstol >= 0 (finite), maxiters >= 0.
+ * Requests are grouped until nls_flush or nls_status, which launch every
+ * pending request of the handle together (one persistent launch for all
+ * thread-tiled requests).  *req receives an id for nls_status.
+ * batch == 0 is a no-op that still returns an id.
+ * Errors: NLS_E_INVALID (null pointers, negative batch/maxiters, bad abstol,
+ * unknown algorithm), NLS_E_UNSUPPORTED (n outside [1, 128], unknown family,
+ * tiling that cannot hold n). */
+int nls_solve(nls_handle h, int family, const double *params, double *u, int n, int64_t batch,
+              int alg, double abstol, int maxiters, const nls_outputs *out, int64_t *req);
+
+/* Launch every pending request of the handle on its stream (asynchronous). */
+int nls_flush(nls_handle h);
+
+/* Completion of request `req`: flushes if needed, then waits up to
+ * timeout_ms on the host (< 0 = no limit, 0 = poll; the device never
+ * waits).  On NLS_OK, *solved (may be NULL) = number of its instances with
+ * status NLS_SUCCESS.  NLS_E_TIMEOUT if not complete yet (query again);
+ * NLS_E_NOTFOUND for an unknown or already released id. */
+int nls_status(nls_handle h, int64_t req, int64_t *solved, int timeout_ms);
+
+/* Synchronous end-to-end variant on HOST buffers: copies params and u
+ * (pinned host memory is fastest) into library-owned device memory, solves,
+ * copies u and the per-instance outputs (HOST pointers in `out`, each may be
+ * NULL) back, and waits.  Same arguments and errors as nls_solve, plus
+ * NLS_E_NOMEM when the staging buffers would exceed the memory cap. */
+int nls_solve_host(nls_handle h, int family, const double *params, double *u, int n,
+                   int64_t batch, int alg, double abstol, int maxiters, const nls_outputs *out,
+                   int64_t *solved);
+
+/* Destroy the context; waits for its outstanding work first. */
+int nls_batch_destroy(nls_handle h);
+
+/* Message of the last error on this handle (or of a failed create when
+ * h == NULL); never NULL. */
+const char *nls_last_error(nls_handle h);
+
+/* Kernels launched by this handle since creation (for launch accounting). */
+int64_t nls_launch_count(nls_handle h);
+
+/* Scheduling options of a handle (apply to later flushes). */
+enum nls_option {
+    NLS_OPT_PERSISTENT = 1,   /* 1 (default): persistent grid of about one wave
+                                 of CTAs pulling instances from a work counter;
+                                 0: one CTA per block of instances             */
+    NLS_OPT_REFILL_BELOW = 2, /* thread tiling, persistent: a warp refills its
+                                 idle lanes when at most this many lanes are
+                                 still iterating (0..31, default 24)           */
+    NLS_OPT_CTAS_PER_SM = 3   /* cap on resident CTAs per SM (0 = occupancy)   */
+};
+/* Errors: NLS_E_INVALID for an unknown option or a value out of range. */
+int nls_set_option(nls_handle h, int option, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NLS_H */

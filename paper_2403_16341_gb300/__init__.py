@@ -1,0 +1,233 @@
+"""Python binding of the GB300 batched nonlinear solver (``include/nls.h``).
+
+The functions named ``nls_*`` are one-to-one ctypes bindings of the C ABI:
+they marshal arguments and nothing else; every step of a solve runs in the
+CUDA kernels of ``_lib/libnls.so``.  ``Solver`` and ``solve`` are small
+conveniences over them for torch tensors (device memory and the current
+stream come from PyTorch).
+
+There is no CPU fallback: if the CUDA library has not been built, or no GPU
+is present, calls raise instead of computing anything elsewhere.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import inputs  # noqa: F401  (seeded workload generator)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libnls.so")
+
+# nls_family
+NLS_CUBIC, NLS_BRATU, NLS_SQUARE, NLS_ROSENBROCK = 0, 1, 2, 3
+# nls_alg and flags
+NLS_NEWTON, NLS_NEWTON_BACKTRACK, NLS_TRUST_DOGLEG = 0, 1, 2
+NLS_ALG_MASK = 0xFF
+NLS_MIXED = 1 << 8
+NLS_ANALYTIC_JAC = 1 << 9
+NLS_TILE_THREAD = 1 << 10
+NLS_TILE_WARP = 1 << 11
+NLS_TILE_CTA = 1 << 12
+# nls_inst_status
+(NLS_SUCCESS, NLS_MAXITERS, NLS_SINGULAR, NLS_NONFINITE, NLS_LS_FAILED, NLS_TR_STALLED,
+ NLS_ABORTED) = range(7)
+# nls_err
+NLS_OK, NLS_E_INVALID, NLS_E_CUDA, NLS_E_NOMEM = 0, -1, -2, -3
+NLS_E_UNSUPPORTED, NLS_E_TIMEOUT, NLS_E_BUSY, NLS_E_NOTFOUND = -4, -5, -6, -7
+# nls_option
+NLS_OPT_PERSISTENT, NLS_OPT_REFILL_BELOW, NLS_OPT_CTAS_PER_SM = 1, 2, 3
+
+EXPORTED = ("nls_batch_create", "nls_solve", "nls_flush", "nls_status", "nls_solve_host",
+            "nls_batch_destroy", "nls_last_error", "nls_launch_count", "nls_set_option")
+
+
+class NlsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"nls error {code}: {msg}")
+        self.code = code
+
+
+class nls_outputs(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_void_p), ("iters", ctypes.c_void_p),
+                ("resid_inf", ctypes.c_void_p), ("nfev", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load ``libnls.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library {p} is missing: build it with "
+                               "paper_2403_16341_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        out_p = ctypes.POINTER(nls_outputs)
+        sig = {
+            "nls_batch_create": ([ctypes.POINTER(vp), i32, vp, ctypes.c_size_t], i32),
+            "nls_solve": ([vp, i32, vp, vp, i32, i64, i32, dbl, i32, out_p,
+                           ctypes.POINTER(i64)], i32),
+            "nls_flush": ([vp], i32),
+            "nls_status": ([vp, i64, ctypes.POINTER(i64), i32], i32),
+            "nls_solve_host": ([vp, i32, vp, vp, i32, i64, i32, dbl, i32, out_p,
+                                ctypes.POINTER(i64)], i32),
+            "nls_batch_destroy": ([vp], i32),
+            "nls_last_error": ([vp], ctypes.c_char_p),
+            "nls_launch_count": ([vp], i64),
+            "nls_set_option": ([vp, i32, i64], i32),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+# ------------------------------------------------------------- raw C ABI
+
+def nls_batch_create(device: int = 0, stream: int = 0, mem_cap_bytes: int = 0) -> int:
+    lib = load_library()
+    h = ctypes.c_void_p()
+    rc = lib.nls_batch_create(ctypes.byref(h), device, ctypes.c_void_p(stream or None),
+                              mem_cap_bytes)
+    if rc:
+        raise NlsError(rc, lib.nls_last_error(None).decode())
+    return h.value
+
+
+def _check(h, rc: int) -> int:
+    if rc:
+        raise NlsError(rc, load_library().nls_last_error(h).decode())
+    return rc
+
+
+def _outs(status=0, iters=0, resid=0, nfev=0):
+    return nls_outputs(status or None, iters or None, resid or None, nfev or None)
+
+
+def nls_solve(h, family, params, u, n, batch, alg, abstol, maxiters, status=0, iters=0,
+              resid_inf=0, nfev=0) -> int:
+    """Enqueue a solve on raw device addresses; returns the request id."""
+    req = ctypes.c_int64()
+    out = _outs(status, iters, resid_inf, nfev)
+    _check(h, load_library().nls_solve(h, family, params or None, u or None, n, batch, alg,
+                                       abstol, maxiters, ctypes.byref(out), ctypes.byref(req)))
+    return req.value
+
+
+def nls_flush(h) -> None:
+    _check(h, load_library().nls_flush(h))
+
+
+def nls_status(h, req: int, timeout_ms: int = -1):
+    """Returns the number of solved instances, or None on NLS_E_TIMEOUT."""
+    s = ctypes.c_int64(-1)
+    rc = load_library().nls_status(h, req, ctypes.byref(s), timeout_ms)
+    if rc == NLS_E_TIMEOUT:
+        return None
+    _check(h, rc)
+    return s.value
+
+
+def nls_solve_host(h, family, params, u, n, batch, alg, abstol, maxiters, status=0, iters=0,
+                   resid_inf=0, nfev=0) -> int:
+    """Synchronous solve on raw HOST addresses; returns the solved count."""
+    s = ctypes.c_int64(-1)
+    out = _outs(status, iters, resid_inf, nfev)
+    _check(h, load_library().nls_solve_host(h, family, params or None, u or None, n, batch, alg,
+                                            abstol, maxiters, ctypes.byref(out), ctypes.byref(s)))
+    return s.value
+
+
+def nls_batch_destroy(h) -> None:
+    _check(h, load_library().nls_batch_destroy(h))
+
+
+def nls_last_error(h) -> str:
+    return load_library().nls_last_error(h).decode()
+
+
+def nls_launch_count(h) -> int:
+    return load_library().nls_launch_count(h)
+
+
+def nls_set_option(h, option: int, value: int) -> None:
+    _check(h, load_library().nls_set_option(h, option, value))
+
+
+# ------------------------------------------------------------- torch helpers
+
+class Solver:
+    """A handle bound to a torch CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None, mem_cap_bytes: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the batched solver has no CPU path")
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.h = nls_batch_create(device, self.stream.cuda_stream, mem_cap_bytes)
+
+    def close(self) -> None:
+        if self.h:
+            nls_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, option: int, value: int) -> None:
+        nls_set_option(self.h, option, value)
+
+    def launches(self) -> int:
+        return nls_launch_count(self.h)
+
+    def submit(self, family: int, params, u, alg: int, abstol: float = 1e-10, maxiters: int = 50,
+               outputs=None) -> int:
+        """Enqueue; ``u`` ([n, B] float64 CUDA, contiguous) is overwritten with the roots.
+        ``outputs`` = (status, iters, resid, nfev) tensors or None."""
+        n, B = u.shape
+        st = it = rs = nf = 0
+        if outputs is not None:
+            st, it, rs, nf = (t.data_ptr() if t is not None else 0 for t in outputs)
+        p = params.data_ptr() if params is not None and params.numel() else 0
+        return nls_solve(self.h, family, p, u.data_ptr(), n, B, alg, abstol, maxiters, st, it,
+                         rs, nf)
+
+    def flush(self) -> None:
+        nls_flush(self.h)
+
+    def wait(self, req: int, timeout_ms: int = -1):
+        return nls_status(self.h, req, timeout_ms)
+
+
+def solve(family: int, params, u0, alg: int = NLS_NEWTON, abstol: float = 1e-10,
+          maxiters: int = 50, solver: Solver | None = None):
+    """Solve a batch held in torch CUDA tensors (params [E, B], u0 [n, B], float64).
+
+    Returns (u, status, iters, resid_inf, nfev, solved)."""
+    import torch
+    s = solver or Solver(u0.device.index or 0)
+    u = u0.detach().clone().contiguous()
+    n, B = u.shape
+    dev = u.device
+    status = torch.empty(B, dtype=torch.int32, device=dev)
+    iters = torch.empty(B, dtype=torch.int32, device=dev)
+    resid = torch.empty(B, dtype=torch.float64, device=dev)
+    nfev = torch.empty(B, dtype=torch.int32, device=dev)
+    p = params.contiguous() if params is not None else None
+    req = s.submit(family, p, u, alg, abstol, maxiters, (status, iters, resid, nfev))
+    solved = s.wait(req)
+    return u, status, iters, resid, nfev, solved

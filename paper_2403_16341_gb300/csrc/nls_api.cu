@@ -1,0 +1,439 @@
+// nls_api.cu -- the C ABI (include/nls.h): handles, argument checks, request
+// grouping, launches, completion.  Every solve step runs in the kernels; this
+// file only validates, allocates library workspace and enqueues.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/nls.h"
+#include "nls_internal.h"
+
+namespace nls {
+KernelInfo thread_kernel_cubic(int n, bool mixed, bool analytic);
+KernelInfo thread_kernel_bratu(int n, bool mixed, bool analytic);
+KernelInfo thread_kernel_square(int n, bool mixed, bool analytic);
+KernelInfo thread_kernel_rosenbrock(int n, bool mixed, bool analytic);
+
+KernelInfo thread_kernel(int family, int n, bool mixed, bool analytic)
+{
+    switch (family) {
+    case FAM_CUBIC: return thread_kernel_cubic(n, mixed, analytic);
+    case FAM_BRATU: return thread_kernel_bratu(n, mixed, analytic);
+    case FAM_SQUARE: return thread_kernel_square(n, mixed, analytic);
+    case FAM_ROSENBROCK: return thread_kernel_rosenbrock(n, mixed, analytic);
+    default: return KernelInfo{};
+    }
+}
+} // namespace nls
+
+// (no `using namespace nls`: its exp overloads must not leak into global lookup)
+using nls::KernelInfo;
+using nls::SolveArgs;
+using nls::FAM_CUBIC;
+using nls::FAM_BRATU;
+using nls::FAM_SQUARE;
+using nls::FAM_ROSENBROCK;
+using nls::thread_kernel;
+
+namespace {
+
+constexpr int RING = 1 << 16; // per-handle device counters (2 per request)
+
+struct Request {
+    int64_t id = 0;
+    SolveArgs args{};
+    KernelInfo kern{};
+    int slot = -1;                         // first of 2 ring entries (solved, work counter)
+    std::shared_ptr<cudaEvent_t> done;     // recorded after the request's group
+    bool launched = false;
+    long long solved_final = -1;           // captured when the ring slot is reused
+};
+
+struct Opts {
+    int persistent = 1;     // persistent grid with a work counter
+    int refill_below = 24;  // refill idle lanes when running lanes <= this
+    int ctas_per_sm = 0;    // 0 = occupancy limit
+};
+
+} // namespace
+
+struct nls_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t mem_cap = 0;
+    size_t mem_used = 0;
+    int sms = 0;
+    std::string err;
+    int64_t next_id = 1;
+    int64_t launches = 0;
+    Opts opt;
+    std::map<int64_t, Request> reqs;
+    std::vector<int64_t> pending;
+    unsigned long long *d_ctr = nullptr; // [RING]
+    unsigned long long *h_ctr = nullptr; // pinned mirror
+    std::vector<int64_t> owner;          // ring slot -> request id (0 = free)
+    int ring_pos = 0;
+    // staging for nls_solve_host
+    void *d_stage = nullptr;
+    size_t stage_bytes = 0;
+};
+
+static std::mutex g_err_mu;
+static std::string g_err;
+
+static int fail(nls_batch *h, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else {
+        std::lock_guard<std::mutex> g(g_err_mu);
+        g_err = buf;
+    }
+    return code;
+}
+
+#define NLS_CUDA(h, call)                                                                      \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail((h), NLS_E_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+    } while (0)
+
+static int n_params(int family, int n)
+{
+    switch (family) {
+    case FAM_CUBIC: return n * n + n;
+    case FAM_BRATU: return 1;
+    case FAM_SQUARE: return n;
+    case FAM_ROSENBROCK: return 0;
+    default: return -1;
+    }
+}
+
+static int dev_alloc(nls_batch *h, void **p, size_t bytes)
+{
+    if (h->mem_cap && h->mem_used + bytes > h->mem_cap)
+        return fail(h, NLS_E_NOMEM, "workspace of %zu bytes exceeds the cap of %zu", h->mem_used + bytes,
+                    h->mem_cap);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(h, NLS_E_NOMEM, "cudaMalloc(%zu) out of memory", bytes);
+    }
+    if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+    h->mem_used += bytes;
+    return NLS_OK;
+}
+
+// Pick the kernel for one request (thread tiling for n <= 8 for now).
+static int select_kernel(nls_batch *h, int family, int n, int alg, KernelInfo *out)
+{
+    const bool mixed = (alg & NLS_MIXED) != 0;
+    const bool analytic = (alg & NLS_ANALYTIC_JAC) != 0;
+    const int tiles = alg & (NLS_TILE_THREAD | NLS_TILE_WARP | NLS_TILE_CTA);
+    if (tiles & ~NLS_TILE_THREAD || n > 8)
+        return fail(h, NLS_E_UNSUPPORTED, "n = %d with tiling 0x%x is not supported by this build", n,
+                    tiles);
+    *out = thread_kernel(family, n, mixed, analytic);
+    if (!out->launch) return fail(h, NLS_E_UNSUPPORTED, "no kernel for family %d, n = %d", family, n);
+    return NLS_OK;
+}
+
+static int wait_event(nls_batch *h, cudaEvent_t ev, int timeout_ms)
+{
+    if (timeout_ms < 0) {
+        NLS_CUDA(h, cudaEventSynchronize(ev));
+        return NLS_OK;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return NLS_OK;
+        if (e != cudaErrorNotReady) return fail(h, NLS_E_CUDA, "cudaEventQuery: %s", cudaGetErrorString(e));
+        auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0)
+                      .count();
+        if (ms >= timeout_ms) return fail(h, NLS_E_TIMEOUT, "request not complete after %d ms", timeout_ms);
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+// Reserve `count` consecutive ring entries; requests still owning them are
+// waited for and their solved counts kept on the host first.
+static int ring_take(nls_batch *h, int count, int *start)
+{
+    if (count > RING) return fail(h, NLS_E_INVALID, "too many requests in one flush (%d)", count / 2);
+    if (h->ring_pos + count > RING) h->ring_pos = 0;
+    const int s = h->ring_pos;
+    for (int i = s; i < s + count; ++i) {
+        const int64_t id = h->owner[i];
+        if (!id) continue;
+        auto it = h->reqs.find(id);
+        if (it != h->reqs.end() && it->second.slot >= 0) {
+            Request &r = it->second;
+            NLS_CUDA(h, cudaEventSynchronize(*r.done));
+            r.solved_final = (long long)h->h_ctr[r.slot];
+            h->owner[r.slot] = h->owner[r.slot + 1] = 0;
+            r.slot = -1;
+        }
+        h->owner[i] = 0;
+    }
+    h->ring_pos = s + count;
+    *start = s;
+    return NLS_OK;
+}
+
+static int flush_pending(nls_batch *h)
+{
+    if (h->pending.empty()) return NLS_OK;
+    const int nreq = (int)h->pending.size();
+    int s0 = 0;
+    int rc = ring_take(h, 2 * nreq, &s0);
+    if (rc) return rc;
+    NLS_CUDA(h, cudaMemsetAsync(h->d_ctr + s0, 0, sizeof(unsigned long long) * 2 * nreq, h->stream));
+    auto ev = std::shared_ptr<cudaEvent_t>(new cudaEvent_t, [](cudaEvent_t *e) {
+        cudaEventDestroy(*e);
+        delete e;
+    });
+    NLS_CUDA(h, cudaEventCreateWithFlags(ev.get(), cudaEventDisableTiming));
+    for (int i = 0; i < nreq; ++i) {
+        Request &r = h->reqs[h->pending[i]];
+        r.slot = s0 + 2 * i;
+        h->owner[r.slot] = h->owner[r.slot + 1] = r.id;
+        r.args.solved = h->d_ctr + r.slot;
+        r.done = ev;
+        r.launched = true;
+        if (r.args.batch == 0) continue;
+        const int64_t ctas = (r.args.batch + r.kern.per_cta - 1) / r.kern.per_cta;
+        int grid = (int)std::min<int64_t>(ctas, INT32_MAX);
+        if (h->opt.persistent) {
+            int occ = 0;
+            NLS_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r.kern.func, r.kern.block,
+                                                                      r.kern.smem));
+            if (h->opt.ctas_per_sm > 0) occ = std::min(occ, h->opt.ctas_per_sm);
+            occ = std::max(occ, 1);
+            grid = (int)std::min<int64_t>(ctas, (int64_t)occ * h->sms);
+            r.args.counter = h->d_ctr + r.slot + 1;
+            r.args.refill_below = h->opt.refill_below;
+        } else {
+            r.args.counter = nullptr;
+            r.args.refill_below = 0;
+        }
+        cudaError_t e = r.kern.launch(r.args, grid, h->stream);
+        if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+        ++h->launches;
+    }
+    NLS_CUDA(h, cudaMemcpyAsync(h->h_ctr + s0, h->d_ctr + s0, sizeof(unsigned long long) * 2 * nreq,
+                                cudaMemcpyDeviceToHost, h->stream));
+    NLS_CUDA(h, cudaEventRecord(*ev, h->stream));
+    h->pending.clear();
+    return NLS_OK;
+}
+
+static int validate(nls_batch *h, int family, const double *params, const double *u, int n, int64_t batch,
+                    int alg, double abstol, int maxiters)
+{
+    if (!h) return NLS_E_INVALID;
+    if (family < 0 || family > FAM_ROSENBROCK) return fail(h, NLS_E_UNSUPPORTED, "unknown family %d", family);
+    if (n < 1 || n > 128) return fail(h, NLS_E_UNSUPPORTED, "n = %d outside [1, 128]", n);
+    if (batch < 0) return fail(h, NLS_E_INVALID, "negative batch");
+    if (maxiters < 0) return fail(h, NLS_E_INVALID, "negative maxiters");
+    if (!(abstol >= 0.0) || !std::isfinite(abstol)) return fail(h, NLS_E_INVALID, "abstol must be finite and >= 0");
+    const int a = alg & NLS_ALG_MASK;
+    if (a > NLS_TRUST_DOGLEG) return fail(h, NLS_E_INVALID, "unknown algorithm %d", a);
+    if (alg & ~(NLS_ALG_MASK | NLS_MIXED | NLS_ANALYTIC_JAC | NLS_TILE_THREAD | NLS_TILE_WARP | NLS_TILE_CTA))
+        return fail(h, NLS_E_INVALID, "unknown flags in alg 0x%x", alg);
+    if (batch > 0 && !u) return fail(h, NLS_E_INVALID, "u is NULL");
+    if (batch > 0 && n_params(family, n) > 0 && !params) return fail(h, NLS_E_INVALID, "params is NULL");
+    return NLS_OK;
+}
+
+extern "C" {
+
+int nls_batch_create(nls_handle *out, int device, void *cuda_stream, size_t mem_cap_bytes)
+{
+    if (!out) return fail(nullptr, NLS_E_INVALID, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return fail(nullptr, NLS_E_CUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+    if (device < 0 || device >= ndev) return fail(nullptr, NLS_E_INVALID, "device %d of %d", device, ndev);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail(nullptr, NLS_E_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    std::unique_ptr<nls_batch> h(new nls_batch);
+    h->device = device;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->mem_cap = mem_cap_bytes;
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
+    int rc = dev_alloc(h.get(), (void **)&h->d_ctr, sizeof(unsigned long long) * RING);
+    if (rc) return fail(nullptr, rc, "%s", h->err.c_str());
+    e = cudaMallocHost((void **)&h->h_ctr, sizeof(unsigned long long) * RING);
+    if (e != cudaSuccess) {
+        cudaFree(h->d_ctr);
+        return fail(nullptr, NLS_E_CUDA, "cudaMallocHost: %s", cudaGetErrorString(e));
+    }
+    h->owner.assign(RING, 0);
+    *out = h.release();
+    return NLS_OK;
+}
+
+int nls_solve(nls_handle h, int family, const double *params, double *u, int n, int64_t batch, int alg,
+              double abstol, int maxiters, const nls_outputs *out, int64_t *req)
+{
+    int rc = validate(h, family, params, u, n, batch, alg, abstol, maxiters);
+    if (rc) return rc;
+    if (!req) return fail(h, NLS_E_INVALID, "req is NULL");
+    Request r;
+    rc = select_kernel(h, family, n, alg, &r.kern);
+    if (rc) return rc;
+    r.id = h->next_id++;
+    r.args.params = params;
+    r.args.u = u;
+    r.args.batch = batch;
+    r.args.n = n;
+    r.args.alg = alg & NLS_ALG_MASK;
+    r.args.abstol = abstol;
+    r.args.maxiters = maxiters;
+    if (out) {
+        r.args.status = out->status;
+        r.args.iters = out->iters;
+        r.args.resid = out->resid_inf;
+        r.args.nfev = out->nfev;
+    }
+    h->reqs[r.id] = r;
+    h->pending.push_back(r.id);
+    *req = r.id;
+    return NLS_OK;
+}
+
+int nls_flush(nls_handle h)
+{
+    if (!h) return NLS_E_INVALID;
+    NLS_CUDA(h, cudaSetDevice(h->device));
+    return flush_pending(h);
+}
+
+int nls_status(nls_handle h, int64_t req, int64_t *solved, int timeout_ms)
+{
+    if (!h) return NLS_E_INVALID;
+    auto it = h->reqs.find(req);
+    if (it == h->reqs.end()) return fail(h, NLS_E_NOTFOUND, "unknown request %lld", (long long)req);
+    NLS_CUDA(h, cudaSetDevice(h->device));
+    if (!it->second.launched) {
+        int rc = flush_pending(h);
+        if (rc) return rc;
+    }
+    Request &r = it->second;
+    int rc = wait_event(h, *r.done, timeout_ms);
+    if (rc) return rc;
+    long long s = r.solved_final;
+    if (r.slot >= 0) {
+        s = (long long)h->h_ctr[r.slot];
+        h->owner[r.slot] = h->owner[r.slot + 1] = 0;
+    }
+    if (solved) *solved = s;
+    h->reqs.erase(it);
+    return NLS_OK;
+}
+
+int nls_solve_host(nls_handle h, int family, const double *params, double *u, int n, int64_t batch, int alg,
+                   double abstol, int maxiters, const nls_outputs *out, int64_t *solved)
+{
+    int rc = validate(h, family, params, u, n, batch, alg, abstol, maxiters);
+    if (rc) return rc;
+    NLS_CUDA(h, cudaSetDevice(h->device));
+    const size_t E = (size_t)n_params(family, n);
+    const size_t bp = E * (size_t)batch * 8, bu = (size_t)n * (size_t)batch * 8, bo = (size_t)batch * 4;
+    const size_t need = bp + bu + 3 * bo + (size_t)batch * 8 + 4 * 256;
+    if (need > h->stage_bytes) {
+        if (h->d_stage) {
+            NLS_CUDA(h, cudaStreamSynchronize(h->stream));
+            cudaFree(h->d_stage);
+            h->mem_used -= h->stage_bytes;
+            h->d_stage = nullptr;
+            h->stage_bytes = 0;
+        }
+        rc = dev_alloc(h, &h->d_stage, need);
+        if (rc) return rc;
+        h->stage_bytes = need;
+    }
+    auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+    char *base = static_cast<char *>(h->d_stage);
+    double *dp = reinterpret_cast<double *>(base);
+    double *du = reinterpret_cast<double *>(base + align(bp));
+    double *dres = reinterpret_cast<double *>(base + align(bp) + align(bu));
+    int32_t *dst = reinterpret_cast<int32_t *>(base + align(bp) + align(bu) + align((size_t)batch * 8));
+    int32_t *dit = dst + align(bo) / 4;
+    int32_t *dnf = dit + align(bo) / 4;
+    if (bp) NLS_CUDA(h, cudaMemcpyAsync(dp, params, bp, cudaMemcpyHostToDevice, h->stream));
+    if (bu) NLS_CUDA(h, cudaMemcpyAsync(du, u, bu, cudaMemcpyHostToDevice, h->stream));
+    nls_outputs dout{out && out->status ? dst : nullptr, out && out->iters ? dit : nullptr,
+                     out && out->resid_inf ? dres : nullptr, out && out->nfev ? dnf : nullptr};
+    int64_t req = 0;
+    rc = nls_solve(h, family, bp ? dp : nullptr, du, n, batch, alg, abstol, maxiters, &dout, &req);
+    if (rc) return rc;
+    rc = flush_pending(h);
+    if (rc) return rc;
+    if (bu) NLS_CUDA(h, cudaMemcpyAsync(u, du, bu, cudaMemcpyDeviceToHost, h->stream));
+    if (out && out->status) NLS_CUDA(h, cudaMemcpyAsync(out->status, dst, bo, cudaMemcpyDeviceToHost, h->stream));
+    if (out && out->iters) NLS_CUDA(h, cudaMemcpyAsync(out->iters, dit, bo, cudaMemcpyDeviceToHost, h->stream));
+    if (out && out->nfev) NLS_CUDA(h, cudaMemcpyAsync(out->nfev, dnf, bo, cudaMemcpyDeviceToHost, h->stream));
+    if (out && out->resid_inf)
+        NLS_CUDA(h, cudaMemcpyAsync(out->resid_inf, dres, (size_t)batch * 8, cudaMemcpyDeviceToHost, h->stream));
+    return nls_status(h, req, solved, -1);
+}
+
+int nls_batch_destroy(nls_handle h)
+{
+    if (!h) return NLS_E_INVALID;
+    cudaSetDevice(h->device);
+    flush_pending(h);
+    cudaStreamSynchronize(h->stream);
+    h->reqs.clear();
+    if (h->d_stage) cudaFree(h->d_stage);
+    if (h->d_ctr) cudaFree(h->d_ctr);
+    if (h->h_ctr) cudaFreeHost(h->h_ctr);
+    delete h;
+    return NLS_OK;
+}
+
+const char *nls_last_error(nls_handle h)
+{
+    if (h) return h->err.c_str();
+    std::lock_guard<std::mutex> g(g_err_mu);
+    return g_err.c_str();
+}
+
+int64_t nls_launch_count(nls_handle h) { return h ? h->launches : 0; }
+
+int nls_set_option(nls_handle h, int option, int64_t value)
+{
+    if (!h) return NLS_E_INVALID;
+    switch (option) {
+    case NLS_OPT_PERSISTENT: h->opt.persistent = value != 0; return NLS_OK;
+    case NLS_OPT_REFILL_BELOW:
+        if (value < 0 || value > 31) return fail(h, NLS_E_INVALID, "refill threshold %lld outside [0, 31]", (long long)value);
+        h->opt.refill_below = (int)value;
+        return NLS_OK;
+    case NLS_OPT_CTAS_PER_SM:
+        if (value < 0 || value > 64) return fail(h, NLS_E_INVALID, "CTAs per SM %lld outside [0, 64]", (long long)value);
+        h->opt.ctas_per_sm = (int)value;
+        return NLS_OK;
+    default: return fail(h, NLS_E_INVALID, "unknown option %d", option);
+    }
+}
+
+} // extern "C"

@@ -1,0 +1,23 @@
+// nls_internal.h -- host-side registry of the solver kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "nls_common.cuh"
+
+namespace nls {
+
+using LaunchFn = cudaError_t (*)(const SolveArgs &, int grid, cudaStream_t);
+
+struct KernelInfo {
+    LaunchFn launch = nullptr;
+    const void *func = nullptr;
+    int block = 0;     // threads per CTA
+    int smem = 0;      // dynamic shared memory bytes
+    int per_cta = 0;   // instances per CTA per round (static grids)
+};
+
+// One instance per thread, compile-time n in 1..8.
+KernelInfo thread_kernel(int family, int n, bool mixed, bool analytic);
+
+} // namespace nls

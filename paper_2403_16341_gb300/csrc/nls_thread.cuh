@@ -1,0 +1,411 @@
+// nls_thread.cuh -- one instance per GPU thread, for n <= 8 (compile-time N).
+//
+// The paper's GPU path (Sec. 3.4) runs one statically sized, non-allocating
+// solver per GPU thread.  Here each lane of a warp owns an instance slot and
+// keeps its state in registers: u and F in FP64, the Jacobian and its LU in
+// FP64 or (NLS_MIXED) FP32.  Parameters are staged once per instance into the
+// lane's own shared-memory column (no block synchronisation is needed).
+//
+// One loop pass per instance is one Newton iteration (Sec. 2.1, Eq. 2): the
+// Jacobian by forward-mode duals (Sec. 2.4) or the analytic formula, LU with
+// partial pivoting (Sec. 3.2), then the step of the chosen globalisation:
+// full step, backtracking on the Armijo condition (Sec. 2.2.1, Eq. 8-9), or
+// the dogleg trust-region step with the ratio test (Sec. 2.2.2, Eq. 12-14).
+// Convergence is ||F||_inf <= abstol (Sec. 2.1).
+//
+// Scheduling: all lanes of a warp execute the same pass in lock step (a
+// per-lane running mask), and in a persistent launch a warp refills its idle
+// lanes from a global work counter whenever the number of running lanes
+// drops to `refill_below` -- the lanes that finished early are given new
+// instances instead of idling until the slowest lane of the warp finishes.
+#pragma once
+
+#include "nls_common.cuh"
+
+namespace nls {
+
+// ---------------------------------------------------------------------------
+// Dense LU with partial pivoting on a register matrix, fused with the
+// elimination of the right-hand side.  Row swaps are selects over the
+// compile-time rows (a dynamic row index would force the matrix into local
+// memory).  Pivot: first index of the largest |a_ik|, i >= k, comparing
+// IEEE bit patterns; a NaN below the diagonal is never chosen and a NaN on
+// the diagonal is kept (the same choices as the comparison |a_ik| > best).
+// On return b holds x = A^-1 b.  Returns false on a zero / non-finite pivot.
+template <int N, class P>
+NLS_DI bool lu_solve(P (&a)[N][N], P (&b)[N])
+{
+    using K = decltype(mag_bits(P(0)));
+    const K inf = inf_bits(P(0));
+    P r[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        K best = mag_bits(a[k][k]);
+        int p = k;
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) {
+            K m = mag_bits(a[i][k]);
+            m = (m > inf) ? K(0) : m;
+            if (m > best) { best = m; p = i; }
+        }
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) {
+            const bool s = (p == i);
+#pragma unroll
+            for (int j = k; j < N; ++j) {
+                P t = a[k][j];
+                a[k][j] = s ? a[i][j] : t;
+                a[i][j] = s ? t : a[i][j];
+            }
+            P t = b[k];
+            b[k] = s ? b[i] : t;
+            b[i] = s ? t : b[i];
+        }
+        const K pm = mag_bits(a[k][k]);
+        if (pm == K(0) || pm >= inf) return false;
+        r[k] = rcp(a[k][k]);
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) {
+            const P l = a[i][k] * r[k];
+#pragma unroll
+            for (int j = k + 1; j < N; ++j) a[i][j] -= l * a[k][j];
+            b[i] -= l * b[k];
+        }
+    }
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        P s = b[i];
+#pragma unroll
+        for (int j = i + 1; j < N; ++j) s -= a[i][j] * b[j];
+        b[i] = s * r[i];
+    }
+    return true;
+}
+
+template <class R>
+struct mask_of;
+template <int M_N, uint32_t M, class T>
+struct mask_of<Dual<M_N, M, T>> {
+    static constexpr uint32_t value = M;
+};
+
+template <int N, int FAM, bool MIXED, bool ANALYTIC>
+struct ThreadSolver {
+    using P = typename std::conditional<MIXED, float, double>::type;
+    using Fm = Family<FAM, N>;
+    static constexpr int E = Fm::E;
+
+    // F(u) in FP64 (all families, all modes)
+    NLS_DI static void residual(const ParamView &pv, const double (&u)[N], double (&F)[N])
+    {
+        static_for<0, N>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            F[i] = Fm::template row<i>(pv, PlainVec<N, double>{u});
+        });
+    }
+
+    // J(u) in the Jacobian precision P
+    NLS_DI static void jacobian(const ParamView &pv, const double (&u)[N], P (&J)[N][N])
+    {
+        P up[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) up[i] = P(u[i]);
+        if constexpr (ANALYTIC) {
+            Fm::template jac_analytic<P>(pv, up, J);
+        } else {
+            static_for<0, N>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                const auto r = Fm::template row<i>(pv, SeedVec<N, P>{up});
+                using R = typename std::decay<decltype(r)>::type;
+                static_for<0, N>([&](auto Jc) {
+                    constexpr int j = decltype(Jc)::value;
+                    J[i][j] = dual_has<R>(j) ? r.d[j] : P(0);
+                });
+            });
+        }
+    }
+
+    template <class R>
+    NLS_DI static constexpr bool dual_has(int j) { return (mask_of<R>::value >> j) & 1u; }
+
+    NLS_DI static double sumsq(const double (&v)[N])
+    {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) s = fma(v[i], v[i], s);
+        return s;
+    }
+
+    // ------------------------------------------------------------ lane state
+    double u[N], F[N], dN[N];
+    P g[N], Jg[N], Fp[N];
+    double fF, Delta;
+    int it, nfev, rej, status;
+    bool need_jac;
+
+    NLS_DI void init(const ParamView &pv, const SolveArgs &a, int64_t k)
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) u[i] = a.u[(int64_t)i * a.batch + k];
+        residual(pv, u, F);
+        nfev = 1;
+        it = 0;
+        rej = 0;
+        Delta = TR_DELTA0;
+        need_jac = true;
+        fF = sumsq(F);
+        const uint64_t m = max_mag_bits(F);
+        if (m >= INF64_BITS) status = ST_NONFINITE;
+        else if (m <= mag_bits(a.abstol)) status = ST_SUCCESS;
+        else if (a.maxiters <= 0) status = ST_MAXITERS;
+        else status = ST_RUNNING;
+    }
+
+    NLS_DI void finish(const SolveArgs &a, int64_t k) const
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) a.u[(int64_t)i * a.batch + k] = u[i];
+        if (a.status) a.status[k] = status;
+        if (a.iters) a.iters[k] = it;
+        if (a.resid) a.resid[k] = bits_to_double(max_mag_bits(F));
+        if (a.nfev) a.nfev[k] = nfev;
+    }
+
+    // One loop pass (Jacobian use) of the chosen algorithm.
+    NLS_DI void pass(const ParamView &pv, const SolveArgs &a)
+    {
+        ++it;
+        if (need_jac) {
+            P J[N][N], b[N];
+            jacobian(pv, u, J);
+#pragma unroll
+            for (int i = 0; i < N; ++i) Fp[i] = P(F[i]);
+            if (a.alg != ALG_NEWTON) {
+                // g = J^T F (gradient of 1/2 ||F||^2), taken before J is factored
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    P s = P(0);
+#pragma unroll
+                    for (int i = 0; i < N; ++i) s = fma(J[i][j], Fp[i], s);
+                    g[j] = s;
+                }
+                if (a.alg == ALG_TRUST_DOGLEG) {
+#pragma unroll
+                    for (int i = 0; i < N; ++i) {
+                        P s = P(0);
+#pragma unroll
+                        for (int j = 0; j < N; ++j) s = fma(J[i][j], g[j], s);
+                        Jg[i] = s;
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < N; ++i) b[i] = -Fp[i];
+            if (!lu_solve<N, P>(J, b)) {
+                status = ST_SINGULAR;
+                return;
+            }
+#pragma unroll
+            for (int i = 0; i < N; ++i) dN[i] = double(b[i]);
+            need_jac = false;
+        }
+
+        if (a.alg == ALG_NEWTON) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) u[i] += dN[i];
+            residual(pv, u, F);
+            ++nfev;
+            need_jac = true;
+        } else if (a.alg == ALG_NEWTON_BACKTRACK) {
+            // slope F^T J dN = g . dN (Eq. 9); phi(alpha) = 1/2 ||F(u + alpha dN)||^2
+            P s = P(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) s = fma(g[i], P(dN[i]), s);
+            const double phi0 = 0.5 * fF;
+            double alpha = 1.0;
+            bool ok = false;
+            for (int m = 0; m < LS_MAX_TRIALS; ++m) {
+                double ut[N], Ft[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) ut[i] = fma(alpha, dN[i], u[i]);
+                residual(pv, ut, Ft);
+                ++nfev;
+                const double fFt = sumsq(Ft);
+                if (max_mag_bits(Ft) < INF64_BITS && 0.5 * fFt <= phi0 + LS_C1 * alpha * double(s)) {
+#pragma unroll
+                    for (int i = 0; i < N; ++i) { u[i] = ut[i]; F[i] = Ft[i]; }
+                    fF = fFt;
+                    ok = true;
+                    break;
+                }
+                alpha *= LS_RHO;
+            }
+            if (!ok) {
+                status = ST_LS_FAILED;
+                return;
+            }
+            need_jac = true;
+        } else {
+            // Powell's dogleg on m(d) = 1/2||F||^2 + d^T J^T F + 1/2 d^T J^T J d, ||d||_2 <= Delta.
+            // J d follows from linearity: J dN = -F, J c = -t J g (c = -t g).
+            double d[N];
+            P Jd[N];
+            const P D2 = P(Delta * Delta);
+            P nN2 = P(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) nN2 = fma(P(dN[i]), P(dN[i]), nN2);
+            if (nN2 <= D2) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) { d[i] = dN[i]; Jd[i] = -Fp[i]; }
+            } else {
+                P gg = P(0), JgJg = P(0);
+#pragma unroll
+                for (int i = 0; i < N; ++i) { gg = fma(g[i], g[i], gg); JgJg = fma(Jg[i], Jg[i], JgJg); }
+                const P t = gg / JgJg; // Cauchy point c = -t g minimises m along -g
+                const P cc = t * t * gg;
+                if (cc >= D2) {
+                    const P sc = P(Delta) / nls_sqrt(gg);
+#pragma unroll
+                    for (int i = 0; i < N; ++i) { d[i] = double(-sc * g[i]); Jd[i] = -sc * Jg[i]; }
+                } else {
+                    P w[N], aa = P(0), bb = P(0);
+#pragma unroll
+                    for (int i = 0; i < N; ++i) {
+                        w[i] = P(dN[i]) + t * g[i];
+                        aa = fma(w[i], w[i], aa);
+                        bb = fma(-t * g[i], w[i], bb);
+                    }
+                    const P q = cc - D2;
+                    const P tau = (-bb + nls_sqrt(bb * bb - aa * q)) / aa;
+#pragma unroll
+                    for (int i = 0; i < N; ++i) {
+                        d[i] = double(fma(tau, w[i], -t * g[i]));
+                        Jd[i] = -(P(1) - tau) * t * Jg[i] - tau * Fp[i];
+                    }
+                }
+            }
+            double ut[N], Ft[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) ut[i] = u[i] + d[i];
+            residual(pv, ut, Ft);
+            ++nfev;
+            const double fFt = sumsq(Ft);
+            // rho = ared / pred (Eq. 14); pred = ||F||^2 - ||F + J d||^2 = -2 F.Jd - ||Jd||^2
+            P FJd = P(0), JdJd = P(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) { FJd = fma(Fp[i], Jd[i], FJd); JdJd = fma(Jd[i], Jd[i], JdJd); }
+            const double pred = double(P(-2) * FJd - JdJd);
+            const double ared = fF - fFt;
+            // pred > 0: rho > 0 <=> ared > 0, rho > eta <=> ared > eta pred (no FP64 divide)
+            if (pred > 0.0 && max_mag_bits(Ft) < INF64_BITS && ared > 0.0) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) { u[i] = ut[i]; F[i] = Ft[i]; }
+                fF = fFt;
+                need_jac = true;
+                rej = 0;
+                if (ared > TR_ETA_EXPAND * pred) Delta = fmin(TR_GROW * Delta, TR_DELTA_MAX);
+            } else {
+                Delta *= TR_SHRINK;
+                if (++rej >= TR_MAX_REJECTIONS) {
+                    status = ST_TR_STALLED;
+                    return;
+                }
+            }
+        }
+        const uint64_t m = max_mag_bits(F);
+        if (m >= INF64_BITS) status = ST_NONFINITE;
+        else if (m <= mag_bits(a.abstol)) status = ST_SUCCESS;
+        else if (it >= a.maxiters) status = ST_MAXITERS;
+    }
+};
+
+constexpr int THREAD_TPB = 32; // one warp per CTA: lanes never wait on each other
+
+template <int N, int FAM, bool MIXED>
+constexpr int thread_smem_bytes()
+{
+    return THREAD_TPB * family_params<FAM>(N) * (8 + (MIXED ? 4 : 0));
+}
+
+template <int N, int FAM, bool MIXED, bool ANALYTIC>
+__global__ void __launch_bounds__(THREAD_TPB) k_solve_thread(SolveArgs a)
+{
+    using S = ThreadSolver<N, FAM, MIXED, ANALYTIC>;
+    constexpr int E = S::E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *sd = reinterpret_cast<double *>(smem_raw);
+    float *sf = reinterpret_cast<float *>(sd + E * THREAD_TPB);
+    const int lane = threadIdx.x;
+    const ParamView pv{sd + lane, sf + lane, THREAD_TPB};
+    const unsigned FULL = 0xffffffffu;
+
+    S s;
+    bool have = false;     // lane holds a running instance
+    bool exhausted = false; // no more work for this warp
+    int64_t k = -1;
+    bool first = true;
+    unsigned long long local_solved = 0;
+
+    for (;;) {
+        const int live = __popc(__ballot_sync(FULL, have));
+        if (!exhausted && live <= a.refill_below) {
+            const bool want = !have;
+            int64_t cand = a.batch;
+            if (a.counter == nullptr) {
+                if (first && want) cand = (int64_t)blockIdx.x * THREAD_TPB + lane;
+            } else {
+                const unsigned m = __ballot_sync(FULL, want);
+                if (want) {
+                    const int leader = __ffs(m) - 1;
+                    unsigned long long base = 0;
+                    if (lane == leader) base = atomicAdd(a.counter, (unsigned long long)__popc(m));
+                    base = __shfl_sync(m, base, leader);
+                    cand = (int64_t)base + __popc(m & ((1u << lane) - 1u));
+                }
+            }
+            first = false;
+            bool got = false;
+            if (want && cand < a.batch) {
+                k = cand;
+#pragma unroll 4
+                for (int e = 0; e < E; ++e) {
+                    const double v = __ldg(a.params + (int64_t)e * a.batch + k);
+                    sd[e * THREAD_TPB + lane] = v;
+                    if constexpr (MIXED) sf[e * THREAD_TPB + lane] = float(v);
+                }
+                s.init(pv, a, k);
+                got = true;
+                if (s.status != ST_RUNNING) {
+                    s.finish(a, k);
+                    local_solved += (s.status == ST_SUCCESS);
+                } else {
+                    have = true;
+                }
+            }
+            // the counter is exhausted (or the static slot is taken) once any
+            // lane asked for work and got none
+            exhausted = (a.counter == nullptr) || __any_sync(FULL, want && !got);
+        }
+        if (!__any_sync(FULL, have)) {
+            if (exhausted) break;
+            continue;
+        }
+        if (have) {
+            s.pass(pv, a);
+            if (s.status != ST_RUNNING) {
+                s.finish(a, k);
+                local_solved += (s.status == ST_SUCCESS);
+                have = false;
+            }
+        }
+    }
+    if (a.solved) {
+        // warp-aggregated count of solved instances
+        unsigned long long t = local_solved;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+        if (lane == 0 && t) atomicAdd(a.solved, t);
+    }
+}
+
+} // namespace nls

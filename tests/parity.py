@@ -1,0 +1,61 @@
+"""Helpers shared by the GPU parity tests: run a Batch through the C ABI
+(via the ctypes binding) and compare with the FP64 oracle."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+
+ORACLE_ALG = {0: O.ALG_NEWTON, 1: O.ALG_NEWTON_BACKTRACK, 2: O.ALG_TRUST_DOGLEG}
+FP64_TOL = 1e-9   # relative to max(1, ||u*||_inf), u* = polished oracle root
+MIXED_TOL = 1e-8
+
+
+def gpu_solve(solver, batch, alg, abstol=1e-10, maxiters=50):
+    import torch
+    import paper_2403_16341_gb300 as nls
+    p = torch.from_numpy(np.ascontiguousarray(batch.params)).cuda() if batch.params.size else None
+    u0 = torch.from_numpy(np.ascontiguousarray(batch.u0)).cuda()
+    u, st, it, rs, nf, solved = nls.solve(batch.family, p, u0, alg, abstol, maxiters, solver)
+    torch.cuda.synchronize()
+    return {"u": u.cpu().numpy(), "status": st.cpu().numpy(), "iters": it.cpu().numpy(),
+            "resid": rs.cpu().numpy(), "nfev": nf.cpu().numpy(), "solved": solved}
+
+
+def oracle_solve(batch, alg, abstol=1e-10, maxiters=50, threads=8):
+    u, st, it, rs, nf = O.solve_batch(batch.family, batch.params, batch.u0,
+                                      ORACLE_ALG[alg & 0xFF], abstol, maxiters, threads=threads)
+    return {"u": u, "status": st, "iters": it, "resid": rs, "nfev": nf}
+
+
+def rel_err(u, ref):
+    scale = np.maximum(1.0, np.abs(ref).max(axis=0))
+    return np.abs(u - ref).max(axis=0) / scale
+
+
+def check_parity(batch, g, o, mixed, abstol=1e-10, polish=True):
+    """Asserts the parity rule; returns the per-instance relative errors of
+    the successful instances."""
+    ok_o = o["status"] == O.ST_SUCCESS
+    ok_g = g["status"] == O.ST_SUCCESS
+    if mixed:
+        assert (ok_g | ~ok_o).all(), "mixed precision lost an instance the oracle solved"
+    else:
+        np.testing.assert_array_equal(g["status"], o["status"])
+    both = ok_g & ok_o
+    ref = o["u"][:, both]
+    if polish and both.any():
+        ref = O.polish_batch(batch.family, batch.params[:, both] if batch.params.size
+                             else np.zeros((0, both.sum())), ref)
+    err = rel_err(g["u"][:, both], ref)
+    tol = MIXED_TOL if mixed else FP64_TOL
+    assert err.size == 0 or err.max() <= tol, f"max rel err {err.max():.3e} > {tol}"
+    # every successful instance: reported and recomputed FP64 residual <= abstol
+    assert (g["resid"][ok_g] <= abstol).all()
+    idx = np.nonzero(ok_g)[0]
+    for k in idx[:: max(1, idx.size // 200)]:
+        p = batch.params[:, k] if batch.params.size else np.zeros(1)
+        F = O.residual(batch.family, p, g["u"][:, k])
+        assert np.abs(F).max() <= abstol
+    assert g["solved"] == int(ok_g.sum())
+    return err
