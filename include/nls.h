@@ -167,6 +167,48 @@ enum nls_option {
 /* Errors: NLS_E_INVALID for an unknown option or a value out of range. */
 int nls_set_option(nls_handle h, int option, int64_t value);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free solve (the paper has no counterpart).
+ *
+ * For callers that cannot allocate device memory: code running inside
+ * another runtime that owns all of the GPU's memory (a plug-in or custom
+ * call of a framework with its own pool, a simulator with a fixed arena),
+ * or a hot path that cannot afford cudaMalloc's implicit device-wide
+ * synchronisation.  It needs no handle and makes no cudaMalloc, cudaFree,
+ * cudaMallocHost or other allocating call.
+ *
+ * Solves up to NLS_NOALLOC_MAX_GROUPS groups, each of one (family, n) with
+ * n <= 8, with the persistent thread-tiled kernel of nls_solve.  Each group
+ * needs two 64-bit counters (its work counter and its solved count); they
+ * live in one static device array of NLS_NOALLOC_MAX_GROUPS * 16 bytes that
+ * every GPU loading the library holds until the process exits.  All calls
+ * share that array and reset the counters they use at the start of the
+ * call, so calls that overlap on the GPU (two streams, two host threads)
+ * race: serialise them.  The first call on a device looks up the array's
+ * device address and caches it; make that first call before any stream
+ * capture.
+ *
+ * Runs on the current device, enqueued on cuda_stream (NULL = legacy
+ * default stream).  Inputs and outputs are the caller's DEVICE pointers,
+ * laid out as for nls_solve.  If `solved` (HOST int64[ngroups]) is not
+ * NULL the call waits for the stream and stores each group's number of
+ * NLS_SUCCESS instances; with NULL it returns once everything is enqueued.
+ * Errors: NLS_E_INVALID (ngroups outside 1..NLS_NOALLOC_MAX_GROUPS, NULL
+ * pointers, bad abstol / maxiters / algorithm), NLS_E_UNSUPPORTED (n > 8,
+ * unknown family, a warp or CTA tiling flag), NLS_E_CUDA; the message is in
+ * nls_last_error(NULL). */
+#define NLS_NOALLOC_MAX_GROUPS 64
+typedef struct nls_group {
+    int family;
+    int n;
+    const double *params; /* DEVICE float64[E * batch] */
+    double *u;            /* DEVICE float64[n * batch], u0 in, iterate out */
+    int64_t batch;
+    nls_outputs out;      /* optional DEVICE outputs, as for nls_solve */
+} nls_group;
+int nls_solve_noalloc(void *cuda_stream, const nls_group *groups, int ngroups, int alg,
+                      double abstol, int maxiters, int64_t *solved);
+
 #ifdef __cplusplus
 }
 #endif

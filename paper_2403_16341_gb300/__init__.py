@@ -40,7 +40,9 @@ NLS_E_UNSUPPORTED, NLS_E_TIMEOUT, NLS_E_BUSY, NLS_E_NOTFOUND = -4, -5, -6, -7
 NLS_OPT_PERSISTENT, NLS_OPT_REFILL_BELOW, NLS_OPT_CTAS_PER_SM = 1, 2, 3
 
 EXPORTED = ("nls_batch_create", "nls_solve", "nls_flush", "nls_status", "nls_solve_host",
-            "nls_batch_destroy", "nls_last_error", "nls_launch_count", "nls_set_option")
+            "nls_batch_destroy", "nls_last_error", "nls_launch_count", "nls_set_option",
+            "nls_solve_noalloc")
+NLS_NOALLOC_MAX_GROUPS = 64
 
 
 class NlsError(RuntimeError):
@@ -52,6 +54,11 @@ class NlsError(RuntimeError):
 class nls_outputs(ctypes.Structure):
     _fields_ = [("status", ctypes.c_void_p), ("iters", ctypes.c_void_p),
                 ("resid_inf", ctypes.c_void_p), ("nfev", ctypes.c_void_p)]
+
+
+class nls_group(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_int), ("n", ctypes.c_int), ("params", ctypes.c_void_p),
+                ("u", ctypes.c_void_p), ("batch", ctypes.c_int64), ("out", nls_outputs)]
 
 
 _lock = threading.Lock()
@@ -83,6 +90,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "nls_last_error": ([vp], ctypes.c_char_p),
             "nls_launch_count": ([vp], i64),
             "nls_set_option": ([vp, i32, i64], i32),
+            "nls_solve_noalloc": ([vp, ctypes.POINTER(nls_group), i32, i32, dbl, i32,
+                                   ctypes.POINTER(i64)], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -162,6 +171,25 @@ def nls_launch_count(h) -> int:
 
 def nls_set_option(h, option: int, value: int) -> None:
     _check(h, load_library().nls_set_option(h, option, value))
+
+
+def nls_solve_noalloc(stream, groups, alg, abstol, maxiters, want_solved=True):
+    """Allocation-free solve of up to NLS_NOALLOC_MAX_GROUPS groups.
+
+    ``groups``: sequence of (family, n, params_ptr, u_ptr, batch,
+    (status_ptr, iters_ptr, resid_ptr, nfev_ptr)) with raw DEVICE addresses
+    (0 = none).  Returns the per-group solved counts (waits for the stream),
+    or None when ``want_solved`` is False (returns after enqueueing)."""
+    arr = (nls_group * max(len(groups), 1))()
+    for i, (fam, n, p, u, b, outs) in enumerate(groups):
+        arr[i] = nls_group(fam, n, p or None, u or None, b, _outs(*outs))
+    solved = (ctypes.c_int64 * max(len(groups), 1))()
+    lib = load_library()
+    rc = lib.nls_solve_noalloc(ctypes.c_void_p(stream or None), arr, len(groups), alg, abstol,
+                               maxiters, solved if want_solved else None)
+    if rc:
+        raise NlsError(rc, lib.nls_last_error(None).decode())
+    return list(solved[:len(groups)]) if want_solved else None
 
 
 # ------------------------------------------------------------- torch helpers

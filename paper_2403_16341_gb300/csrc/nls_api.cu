@@ -106,6 +106,8 @@ static int fail(nls_batch *h, int code, const char *fmt, ...)
     return code;
 }
 
+int nls::set_global_error(int code, const char *msg) { return fail(nullptr, code, "%s", msg); }
+
 #define NLS_CUDA(h, call)                                                                      \
     do {                                                                                       \
         cudaError_t e_ = (call);                                                               \

@@ -20,4 +20,7 @@ struct KernelInfo {
 // One instance per thread, compile-time n in 1..8.
 KernelInfo thread_kernel(int family, int n, bool mixed, bool analytic);
 
+// Record a handle-free error message for nls_last_error(NULL); returns code.
+int set_global_error(int code, const char *msg);
+
 } // namespace nls
