@@ -160,6 +160,56 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def extras(args, nls, solver, batch, params, u0, stream, dev):
+    """The FP64-Newton comparison bar and the end-to-end (host buffer) leg."""
+    import torch
+    B = batch.batch
+    # the comparison bar: plain FP64 Newton, one static thread per instance
+    solver.set_option(nls.NLS_OPT_PERSISTENT, 0)
+    ub = torch.empty_like(u0)
+    bo = tuple(torch.empty(B, dtype=dt, device=dev) for dt in
+               (torch.int32, torch.int32, torch.float64, torch.int32))
+    bt = []
+    for r in range(4):
+        ub.copy_(u0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        req = solver.submit(batch.family, params, ub, NEWTON, ABSTOL, MAXITERS, bo)
+        solver.flush()
+        e1.record(stream)
+        sb = solver.wait(req)
+        torch.cuda.synchronize()
+        if r:
+            bt.append(e0.elapsed_time(e1))
+    solver.set_option(nls.NLS_OPT_PERSISTENT, 1)
+    baseline = {"kernel": "plain FP64 Newton, one thread per instance, static grid",
+                "ms": float(np.median(bt)), "solved_per_s": sb / (float(np.median(bt)) / 1e3)}
+
+    # end to end through the C ABI on pinned host buffers
+    hp = torch.from_numpy(batch.params).pin_memory()
+    hu0 = torch.from_numpy(batch.u0).pin_memory()
+    hu = torch.empty_like(hu0).pin_memory()
+    hst = torch.empty(B, dtype=torch.int32).pin_memory()
+    e2e_times, e2e_solved = [], 0
+    for r in range(2 + args.steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ssum = 0
+        for _, alg in VARIANTS:
+            hu.copy_(hu0)
+            ssum += nls.nls_solve_host(solver.h, batch.family, hp.data_ptr(), hu.data_ptr(), N_SYS,
+                                       B, alg, ABSTOL, MAXITERS, hst.data_ptr(), 0, 0, 0)
+        dt = time.perf_counter() - t
+        if r >= 2:
+            e2e_times.append(dt)
+            e2e_solved += ssum
+    e2e = {"value": e2e_solved / sum(e2e_times), "unit": "solved systems/s",
+           "h2d_bytes_per_step": len(VARIANTS) * (hp.numel() + hu0.numel()) * 8,
+           "d2h_bytes_per_step": len(VARIANTS) * (hu.numel() * 8 + B * 4)}
+
+    return baseline, e2e
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_2403_16341_gb300 as nls
@@ -174,7 +224,7 @@ def run_ours(args, world, rank, local):
     solver = nls.Solver(local, stream)
 
     # every rank solves its own 2^20 instances (weak scaling, no exchange)
-    batch = I.cubic_batch(N_SYS, B_FULL, seed=rank, config_id=1, b_half_width=5.0)
+    batch = I.cubic_batch(N_SYS, args.instances, seed=rank, config_id=1, b_half_width=5.0)
     params = torch.from_numpy(batch.params).to(dev)
     u0 = torch.from_numpy(batch.u0).to(dev)
     us = [torch.empty_like(u0) for _ in VARIANTS]
@@ -252,48 +302,9 @@ def run_ours(args, world, rank, local):
             dom, dom_ms = name, ms
     dv = variants[dom]
 
-    # the comparison bar: plain FP64 Newton, one static thread per instance
-    solver.set_option(nls.NLS_OPT_PERSISTENT, 0)
-    ub = torch.empty_like(u0)
-    bo = tuple(torch.empty(B, dtype=dt, device=dev) for dt in
-               (torch.int32, torch.int32, torch.float64, torch.int32))
-    bt = []
-    for r in range(4):
-        ub.copy_(u0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        req = solver.submit(batch.family, params, ub, NEWTON, ABSTOL, MAXITERS, bo)
-        solver.flush()
-        e1.record(stream)
-        sb = solver.wait(req)
-        torch.cuda.synchronize()
-        if r:
-            bt.append(e0.elapsed_time(e1))
-    solver.set_option(nls.NLS_OPT_PERSISTENT, 1)
-    baseline = {"kernel": "plain FP64 Newton, one thread per instance, static grid",
-                "ms": float(np.median(bt)), "solved_per_s": sb / (float(np.median(bt)) / 1e3)}
-
-    # end to end through the C ABI on pinned host buffers
-    hp = torch.from_numpy(batch.params).pin_memory()
-    hu0 = torch.from_numpy(batch.u0).pin_memory()
-    hu = torch.empty_like(hu0).pin_memory()
-    hst = torch.empty(B, dtype=torch.int32).pin_memory()
-    e2e_times, e2e_solved = [], 0
-    for r in range(2 + args.steps):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        ssum = 0
-        for _, alg in VARIANTS:
-            hu.copy_(hu0)
-            ssum += nls.nls_solve_host(solver.h, batch.family, hp.data_ptr(), hu.data_ptr(), N_SYS,
-                                       B, alg, ABSTOL, MAXITERS, hst.data_ptr(), 0, 0, 0)
-        dt = time.perf_counter() - t
-        if r >= 2:
-            e2e_times.append(dt)
-            e2e_solved += ssum
-    e2e = {"value": e2e_solved / sum(e2e_times), "unit": "solved systems/s",
-           "h2d_bytes_per_step": len(VARIANTS) * (hp.numel() + hu0.numel()) * 8,
-           "d2h_bytes_per_step": len(VARIANTS) * (hu.numel() * 8 + B * 4)}
+    baseline, e2e = None, None
+    if not args.no_extras:
+        baseline, e2e = extras(args, nls, solver, batch, params, u0, stream, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -345,8 +356,22 @@ def main():
     ap.add_argument("--sample", type=int, default=1 << 18,
                     help="instances the CPU oracle solves per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", default="",
+                    help="comma-separated subset of the step's variants (profiling runs)")
+    ap.add_argument("--instances", type=int, default=B_FULL,
+                    help="batch size (profiling runs; the benchmark uses 2^20)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64-Newton bar, the end-to-end leg and the CPU baseline")
     args = ap.parse_args()
     world, rank, local = dist_env()
+    if args.variants:
+        keep = set(args.variants.split(","))
+        unknown = keep - {v for v, _ in VARIANTS}
+        if unknown:
+            ap.error(f"unknown variants {sorted(unknown)}")
+        VARIANTS[:] = [v for v in VARIANTS if v[0] in keep]
+    if args.no_extras:
+        args.no_cpu_baseline = True
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:
