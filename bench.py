@@ -111,6 +111,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def dram_traffic(variant: str):
+    """DRAM bytes per launch of `variant` from the committed ncu summary, or
+    None when the kernel sources changed after the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "counters_thread_cubic_n8.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) == 3 and parts[0] == variant:
+            rev = parts[2]
+            try:
+                changed = subprocess.run(
+                    ["git", "-C", ROOT, "diff", "--quiet", rev, "--", "paper_2403_16341_gb300/csrc"],
+                    capture_output=True).returncode
+            except OSError:
+                return None
+            return int(parts[1]) if changed == 0 else None
+    return None
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -315,13 +335,7 @@ def run_ours(args, world, rank, local):
                "sample": f"first {sample} of the 2^20 instances, NR+backtracking and TR-dogleg "
                          f"in FP64 ({dt:.1f} s)"}
 
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    traffic = None
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get(dom)
-        except Exception:
-            traffic = None
+    traffic = dram_traffic(dom)
     achieved = dv["fp64_tflops"]
     if rank == 0:
         line = {

@@ -34,6 +34,15 @@ KernelInfo thread_kernel(int family, int n, bool mixed, bool analytic)
     default: return KernelInfo{};
     }
 }
+KernelInfo warp_kernel_fp64(int family, int L);
+KernelInfo warp_kernel_mixed(int family, int L);
+
+KernelInfo warp_kernel(int family, int n, bool mixed, int lanes)
+{
+    int L = lanes ? lanes : (n <= 8 ? 8 : n <= 16 ? 16 : 32);
+    if (n > L || n > 32) return KernelInfo{};
+    return mixed ? warp_kernel_mixed(family, L) : warp_kernel_fp64(family, L);
+}
 } // namespace nls
 
 // (no `using namespace nls`: its exp overloads must not leak into global lookup)
@@ -44,6 +53,7 @@ using nls::FAM_BRATU;
 using nls::FAM_SQUARE;
 using nls::FAM_ROSENBROCK;
 using nls::thread_kernel;
+using nls::warp_kernel;
 
 namespace {
 
@@ -141,16 +151,25 @@ static int dev_alloc(nls_batch *h, void **p, size_t bytes)
     return NLS_OK;
 }
 
-// Pick the kernel for one request (thread tiling for n <= 8 for now).
+// Pick the kernel for one request: a forced tiling flag, else thread (n <= 8),
+// warp (n <= 32) or CTA (n <= 128).
 static int select_kernel(nls_batch *h, int family, int n, int alg, KernelInfo *out)
 {
     const bool mixed = (alg & NLS_MIXED) != 0;
     const bool analytic = (alg & NLS_ANALYTIC_JAC) != 0;
-    const int tiles = alg & (NLS_TILE_THREAD | NLS_TILE_WARP | NLS_TILE_CTA);
-    if (tiles & ~NLS_TILE_THREAD || n > 8)
-        return fail(h, NLS_E_UNSUPPORTED, "n = %d with tiling 0x%x is not supported by this build", n,
-                    tiles);
-    *out = thread_kernel(family, n, mixed, analytic);
+    int tiles = alg & (NLS_TILE_THREAD | NLS_TILE_WARP | NLS_TILE_CTA);
+    if (tiles && (tiles & (tiles - 1)))
+        return fail(h, NLS_E_INVALID, "more than one tiling flag in alg 0x%x", alg);
+    if (!tiles) tiles = n <= 8 ? NLS_TILE_THREAD : n <= 32 ? NLS_TILE_WARP : NLS_TILE_CTA;
+    if (tiles == NLS_TILE_THREAD) {
+        if (n > 8) return fail(h, NLS_E_UNSUPPORTED, "thread tiling holds n <= 8 (n = %d)", n);
+        *out = thread_kernel(family, n, mixed, analytic);
+    } else if (tiles == NLS_TILE_WARP) {
+        if (n > 32) return fail(h, NLS_E_UNSUPPORTED, "warp tiling holds n <= 32 (n = %d)", n);
+        *out = warp_kernel(family, n, mixed, 0);
+    } else {
+        return fail(h, NLS_E_UNSUPPORTED, "CTA tiling (n = %d) is not available", n);
+    }
     if (!out->launch) return fail(h, NLS_E_UNSUPPORTED, "no kernel for family %d, n = %d", family, n);
     return NLS_OK;
 }

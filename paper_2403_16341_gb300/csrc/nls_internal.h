@@ -24,3 +24,9 @@ KernelInfo thread_kernel(int family, int n, bool mixed, bool analytic);
 int set_global_error(int code, const char *msg);
 
 } // namespace nls
+
+namespace nls {
+// One instance per warp segment of L = 8, 16 or 32 lanes (the smallest L >= n,
+// or `lanes` when non-zero), runtime n <= L.
+KernelInfo warp_kernel(int family, int n, bool mixed, int lanes = 0);
+} // namespace nls
