@@ -16,6 +16,7 @@ host cores over a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -111,6 +112,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+THREAD_KERNEL_SOURCES = ("nls_dual.cuh", "nls_common.cuh", "nls_thread.cuh",
+                         "nls_thread_kernels.cuh", "nls_thread_cubic.cu")
+
+
+def thread_kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in THREAD_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2403_16341_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def dram_traffic(variant: str):
     """DRAM bytes per launch of `variant` from the committed ncu summary, or
     None when the kernel sources changed after the counters were taken."""
@@ -120,14 +133,7 @@ def dram_traffic(variant: str):
     for line in open(path):
         parts = line.split()
         if len(parts) == 3 and parts[0] == variant:
-            rev = parts[2]
-            try:
-                changed = subprocess.run(
-                    ["git", "-C", ROOT, "diff", "--quiet", rev, "--", "paper_2403_16341_gb300/csrc"],
-                    capture_output=True).returncode
-            except OSError:
-                return None
-            return int(parts[1]) if changed == 0 else None
+            return int(parts[1]) if parts[2] == thread_kernel_hash() else None
     return None
 
 
