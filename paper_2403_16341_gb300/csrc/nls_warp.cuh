@@ -385,31 +385,32 @@ struct WarpSolver {
                 }
             }
         } else {
+            // Every reduction is taken by all segments of the warp before any
+            // per-segment branch (segments of one warp may take different
+            // dogleg branches; a collective inside a branch would diverge).
             const P D2 = P(Delta * Delta);
             const P nN2 = seg_sum<L>(P(dN) * P(dN), 0xffffffffu);
+            const P gg = seg_sum<L>(g * g, 0xffffffffu);
+            const P JgJg = seg_sum<L>(Jg * Jg, 0xffffffffu);
+            const P t = gg / JgJg; // Cauchy point c = -t g minimises the model along -g
+            const P cc = t * t * gg;
+            const P w = P(dN) + t * g; // dN - c
+            const P aa = seg_sum<L>(w * w, 0xffffffffu);
+            const P bb = seg_sum<L>(-t * g * w, 0xffffffffu);
             double d;
             P Jd;
             if (nN2 <= D2) {
                 d = dN;
                 Jd = -Fp;
+            } else if (cc >= D2) {
+                const P sc = P(Delta) / nls_sqrt(gg);
+                d = double(-sc * g);
+                Jd = -sc * Jg;
             } else {
-                const P gg = seg_sum<L>(g * g, 0xffffffffu);
-                const P JgJg = seg_sum<L>(Jg * Jg, 0xffffffffu);
-                const P t = gg / JgJg;
-                const P cc = t * t * gg;
-                if (cc >= D2) {
-                    const P sc = P(Delta) / nls_sqrt(gg);
-                    d = double(-sc * g);
-                    Jd = -sc * Jg;
-                } else {
-                    const P w = P(dN) + t * g;
-                    const P aa = seg_sum<L>(w * w, 0xffffffffu);
-                    const P bb = seg_sum<L>(-t * g * w, 0xffffffffu);
-                    const P q = cc - D2;
-                    const P tau = (-bb + nls_sqrt(bb * bb - aa * q)) / aa;
-                    d = double(fma(tau, w, -t * g));
-                    Jd = -(P(1) - tau) * t * Jg - tau * Fp;
-                }
+                const P q = cc - D2;
+                const P tau = (-bb + nls_sqrt(bb * bb - aa * q)) / aa;
+                d = double(fma(tau, w, -t * g));
+                Jd = -(P(1) - tau) * t * Jg - tau * Fp;
             }
             if (!row_live()) {
                 d = 0.0;
