@@ -37,6 +37,14 @@ KernelInfo thread_kernel(int family, int n, bool mixed, bool analytic)
 KernelInfo warp_kernel_fp64(int family, int L);
 KernelInfo warp_kernel_mixed(int family, int L);
 
+KernelInfo cta_kernel_fp64(int family, int n);
+KernelInfo cta_kernel_mixed(int family, int n);
+
+KernelInfo cta_kernel(int family, int n, bool mixed)
+{
+    return mixed ? cta_kernel_mixed(family, n) : cta_kernel_fp64(family, n);
+}
+
 KernelInfo warp_kernel(int family, int n, bool mixed, int lanes)
 {
     int L = lanes ? lanes : (n <= 8 ? 8 : n <= 16 ? 16 : 32);
@@ -54,6 +62,7 @@ using nls::FAM_SQUARE;
 using nls::FAM_ROSENBROCK;
 using nls::thread_kernel;
 using nls::warp_kernel;
+using nls::cta_kernel;
 
 namespace {
 
@@ -168,7 +177,7 @@ static int select_kernel(nls_batch *h, int family, int n, int alg, KernelInfo *o
         if (n > 32) return fail(h, NLS_E_UNSUPPORTED, "warp tiling holds n <= 32 (n = %d)", n);
         *out = warp_kernel(family, n, mixed, 0);
     } else {
-        return fail(h, NLS_E_UNSUPPORTED, "CTA tiling (n = %d) is not available", n);
+        *out = cta_kernel(family, n, mixed);
     }
     if (!out->launch) return fail(h, NLS_E_UNSUPPORTED, "no kernel for family %d, n = %d", family, n);
     return NLS_OK;

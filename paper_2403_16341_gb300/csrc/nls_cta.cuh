@@ -1,0 +1,540 @@
+// nls_cta.cuh -- one instance per CTA, for 32 < n <= 128 (any n <= 16 R).
+//
+// 256 threads form a 16 x 16 grid.  Thread (ty, tx) keeps, in registers,
+// the R x R block-cyclic tile of the Jacobian with rows ty + 16 a and
+// columns tx + 16 b (a, b < R), in FP64 or (NLS_MIXED) FP32, so the rank-1
+// updates of the LU run out of registers at FMA rate; only the pivot
+// column's multipliers and the pivot row cross threads, through shared
+// memory.  Vectors (u, F, the Newton step, the gradient) live in shared
+// memory, component t with thread t.
+//
+// LU with partial pivoting (Sec. 3.2), rows never move: every row carries
+// the position it would have after the interchanges, and the pivot at step
+// k is the first position >= k holding the largest |a_ik| (the choice an
+// explicit-swap LU makes).  Step k: the 16 owners of column k post their
+// best candidate; after a barrier every thread reduces the 16 candidates,
+// the owners write the multipliers, the owners of the pivot row write it;
+// after a second barrier all threads update their tiles.  The right-hand
+// side is eliminated alongside; back substitution walks the positions down.
+//
+// The Jacobian tile comes from forward-mode duals over the stencil of each
+// owned row (Sec. 2.4).  The globalisations are those of the other tilings.
+#pragma once
+
+#include <climits>
+
+#include "nls_common.cuh"
+
+namespace nls {
+
+constexpr int CTA_T = 16;
+constexpr int CTA_TPB = CTA_T * CTA_T;
+constexpr int CTA_NMAX = 128;
+
+template <bool MIXED>
+struct CtaSmem {
+    using P = typename std::conditional<MIXED, float, double>::type;
+    double u[CTA_NMAX], F[CTA_NMAX], dN[CTA_NMAX], ut[CTA_NMAX], Ft[CTA_NMAX];
+    P Fp[CTA_NMAX], g[CTA_NMAX], Jg[CTA_NMAX], rhs[CTA_NMAX], lcol[CTA_NMAX], prow[CTA_NMAX];
+    P rdiag[CTA_NMAX], x[CTA_NMAX];
+    P red[CTA_T][CTA_NMAX]; // partial sums of J^T F and J g
+    int pos_row[CTA_NMAX];  // row holding pivot position k
+    uint64_t ckey[CTA_T];
+    int cpos[CTA_T], crow[CTA_T];
+    P cval[CTA_T];
+    double rd[CTA_TPB / 32];
+    uint64_t rm[CTA_TPB / 32];
+    long long inst;
+};
+
+template <int R, int FAM, bool MIXED>
+struct CtaSolver {
+    using P = typename std::conditional<MIXED, float, double>::type;
+    using K = decltype(mag_bits(P(0)));
+    using SM = CtaSmem<MIXED>;
+
+    int tid, ty, tx, lane, warp, n;
+    int64_t B, k;
+    const double *params;
+    double lam; // Bratu lambda
+    double fF, Delta;
+    int it, nfev, rej, status;
+    bool need_jac;
+    uint64_t fmag;
+
+    NLS_DI int row(int a) const { return ty + CTA_T * a; }
+    NLS_DI int col(int b) const { return tx + CTA_T * b; }
+
+    // ------------------------------------------------------------ reductions
+    NLS_DI double bsum(double v, SM &sm) const
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sm.rd[warp] = v;
+        __syncthreads();
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < CTA_TPB / 32; ++w) s += sm.rd[w];
+        __syncthreads();
+        return s;
+    }
+    NLS_DI float bsum(float v, SM &sm) const { return float(bsum(double(v), sm)); }
+    NLS_DI uint64_t bmax(uint64_t v, SM &sm) const
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = w > v ? w : v;
+        }
+        if (lane == 0) sm.rm[warp] = v;
+        __syncthreads();
+        uint64_t m = 0;
+#pragma unroll
+        for (int w = 0; w < CTA_TPB / 32; ++w) m = sm.rm[w] > m ? sm.rm[w] : m;
+        __syncthreads();
+        return m;
+    }
+
+    // ------------------------------------------------------------ residual
+    // F_t(x) in FP64 for t < n, x in shared memory; returns F_t (0 for t >= n)
+    NLS_DI double residual_t(const double *x) const
+    {
+        const int t = tid;
+        if (t >= n) return 0.0;
+        const double xt = x[t];
+        if constexpr (FAM == FAM_CUBIC) {
+            double s = 0.0;
+            for (int j = 0; j < n; ++j) s = fma(__ldg(params + (int64_t)(t * n + j) * B + k), x[j], s);
+            return s + xt * xt * xt - __ldg(params + (int64_t)(n * n + t) * B + k);
+        } else if constexpr (FAM == FAM_BRATU) {
+            const double inv_h2 = double((n + 1) * (n + 1));
+            const double left = t > 0 ? x[t - 1] : 0.0;
+            const double right = t < n - 1 ? x[t + 1] : 0.0;
+            return inv_h2 * ((left + (-2.0) * xt) + right) + lam * exp(xt);
+        } else if constexpr (FAM == FAM_SQUARE) {
+            return xt * xt - __ldg(params + (int64_t)t * B + k);
+        } else {
+            return t == 0 ? 1.0 - xt : 10.0 * (xt - x[t - 1] * x[t - 1]);
+        }
+    }
+
+    // ------------------------------------------------------------ Jacobian tile
+    NLS_DI void jacobian_tile(P (&a)[R][R], const SM &sm) const
+    {
+#pragma unroll
+        for (int aa = 0; aa < R; ++aa) {
+            const int i = row(aa);
+            const bool live = i < n;
+            const P ui = live ? P(sm.u[i]) : P(0);
+            // partials of F_i over its stencil: d0 (i-1), d1 (i), d2 (i+1)
+            P d0 = P(0), d1 = P(0), d2 = P(0);
+            if constexpr (FAM == FAM_CUBIC) {
+                const auto x = seed<1, 0, P>(ui);
+                d1 = (x * x * x).d[0];
+            } else if constexpr (FAM == FAM_BRATU) {
+                const P inv_h2 = P((n + 1) * (n + 1));
+                const auto xl = seed<3, 0, P>(P(0));
+                const auto xc = seed<3, 1, P>(ui);
+                const auto xr = seed<3, 2, P>(P(0));
+                const auto f = inv_h2 * ((xl + P(-2) * xc) + xr) + P(lam) * exp(xc);
+                d0 = f.d[0];
+                d1 = f.d[1];
+                d2 = f.d[2];
+            } else if constexpr (FAM == FAM_SQUARE) {
+                const auto x = seed<1, 0, P>(ui);
+                d1 = (x * x).d[0];
+            } else {
+                const P ul = (live && i > 0) ? P(sm.u[i - 1]) : P(0);
+                const auto xl = seed<2, 0, P>(ul);
+                const auto xc = seed<2, 1, P>(ui);
+                const auto f = P(10) * (xc - xl * xl);
+                d0 = f.d[0];
+                d1 = (i == 0) ? P(-1) : f.d[1];
+            }
+#pragma unroll
+            for (int bb = 0; bb < R; ++bb) {
+                const int j = col(bb);
+                P v = P(0);
+                if (live && j < n) {
+                    if constexpr (FAM == FAM_CUBIC) {
+                        // linear part's coefficient, plus d(u_i^3)/du_i on the diagonal
+                        v = P(__ldg(params + (int64_t)(i * n + j) * B + k));
+                        if (j == i) v += d1;
+                    } else {
+                        // stencil families: row i depends on u_{i-1}, u_i, u_{i+1} only
+                        if (j == i - 1) v = d0;
+                        else if (j == i) v = d1;
+                        else if (j == i + 1) v = d2;
+                    }
+                }
+                a[aa][bb] = v;
+            }
+        }
+    }
+
+    // ------------------------------------------------------------ LU
+    // Solves J x = rhs (rhs in sm.rhs, x to sm.x); returns false on a zero or
+    // non-finite pivot (uniform over the CTA).
+    NLS_DI bool lu_solve(P (&a)[R][R], SM &sm) const
+    {
+        const K inf = inf_bits(P(0));
+        int mypos[R];
+#pragma unroll
+        for (int aa = 0; aa < R; ++aa) mypos[aa] = row(aa);
+        bool ok = true;
+#pragma unroll
+        for (int b = 0; b < R; ++b) {
+            for (int c = 0; c < CTA_T; ++c) {
+                const int kk = CTA_T * b + c;
+                if (kk >= n) break;
+                if (tx == c) {
+                    K best = 0;
+                    int bpos = INT_MAX, brow = -1;
+                    P bval = P(0);
+#pragma unroll
+                    for (int aa = 0; aa < R; ++aa) {
+                        const int i = row(aa);
+                        if (i < n && mypos[aa] >= kk) {
+                            K m = mag_bits(a[aa][b]);
+                            if (mypos[aa] > kk && m > inf) m = K(0);
+                            if (brow < 0 || m > best || (m == best && mypos[aa] < bpos)) {
+                                best = m;
+                                bpos = mypos[aa];
+                                brow = i;
+                                bval = a[aa][b];
+                            }
+                        }
+                    }
+                    sm.ckey[ty] = best;
+                    sm.cpos[ty] = bpos;
+                    sm.crow[ty] = brow;
+                    sm.cval[ty] = bval;
+                }
+                __syncthreads(); // S1
+                uint64_t best = 0;
+                int bpos = INT_MAX, prow_i = -1;
+                P pv = P(0);
+#pragma unroll
+                for (int q = 0; q < CTA_T; ++q) {
+                    const int cr = sm.crow[q];
+                    if (cr < 0) continue;
+                    const uint64_t ck = sm.ckey[q];
+                    const int cp = sm.cpos[q];
+                    if (prow_i < 0 || ck > best || (ck == best && cp < bpos)) {
+                        best = ck;
+                        bpos = cp;
+                        prow_i = cr;
+                        pv = sm.cval[q];
+                    }
+                }
+                if (best == 0 || best >= (uint64_t)inf) ok = false;
+                const P r = rcp(pv);
+                bool rem[R];
+#pragma unroll
+                for (int aa = 0; aa < R; ++aa) {
+                    rem[aa] = row(aa) < n && mypos[aa] >= kk && row(aa) != prow_i;
+                    if (tx == c && row(aa) < n) sm.lcol[row(aa)] = rem[aa] ? a[aa][b] * r : P(0);
+                }
+                if (ty == (prow_i & (CTA_T - 1))) {
+                    const int ap = prow_i / CTA_T;
+#pragma unroll
+                    for (int bb = b; bb < R; ++bb) {
+                        P v = P(0);
+#pragma unroll
+                        for (int aa = 0; aa < R; ++aa) v = (aa == ap) ? a[aa][bb] : v;
+                        sm.prow[col(bb)] = v;
+                    }
+                }
+                if (tid == 0) {
+                    sm.pos_row[kk] = prow_i;
+                    sm.rdiag[kk] = r;
+                }
+#pragma unroll
+                for (int aa = 0; aa < R; ++aa) {
+                    if (row(aa) == prow_i) mypos[aa] = kk;
+                    else if (mypos[aa] == kk) mypos[aa] = bpos;
+                }
+                __syncthreads(); // S2
+#pragma unroll
+                for (int aa = 0; aa < R; ++aa) {
+                    if (!rem[aa]) continue;
+                    const P l = sm.lcol[row(aa)];
+#pragma unroll
+                    for (int bb = b; bb < R; ++bb) {
+                        if (bb > b || tx > c) a[aa][bb] -= l * sm.prow[col(bb)];
+                    }
+                }
+                if (tid < n && tid != prow_i) {
+                    // rows still to be pivoted have lcol != 0 only where needed
+                    sm.rhs[tid] -= sm.lcol[tid] * sm.rhs[prow_i];
+                }
+                // the next S1 orders these reads before lcol / prow are rewritten
+            }
+        }
+        __syncthreads();
+        // back substitution over positions n-1 .. 0
+#pragma unroll
+        for (int b = R - 1; b >= 0; --b) {
+            for (int c = CTA_T - 1; c >= 0; --c) {
+                const int kk = CTA_T * b + c;
+                if (kk >= n) continue;
+                if (tid == 0) {
+                    const int p = sm.pos_row[kk];
+                    sm.x[kk] = sm.rhs[p] * sm.rdiag[kk];
+                }
+                __syncthreads();
+                const P xk = sm.x[kk];
+                if (tx == c) {
+#pragma unroll
+                    for (int aa = 0; aa < R; ++aa)
+                        if (row(aa) < n && mypos[aa] < kk) sm.rhs[row(aa)] -= a[aa][b] * xk;
+                }
+                __syncthreads();
+            }
+        }
+        return ok;
+    }
+
+    // ------------------------------------------------------------ driver
+    NLS_DI void set_status_from(uint64_t m, const SolveArgs &A)
+    {
+        fmag = m;
+        if (m >= INF64_BITS) status = ST_NONFINITE;
+        else if (m <= mag_bits(A.abstol)) status = ST_SUCCESS;
+        else if (it >= A.maxiters) status = ST_MAXITERS;
+    }
+
+    NLS_DI void init(const SolveArgs &A, SM &sm)
+    {
+        if (tid < n) sm.u[tid] = A.u[(int64_t)tid * B + k];
+        lam = (FAM == FAM_BRATU) ? __ldg(A.params + k) : 0.0;
+        __syncthreads();
+        const double f = residual_t(sm.u);
+        if (tid < n) sm.F[tid] = f;
+        nfev = 1;
+        it = 0;
+        rej = 0;
+        Delta = TR_DELTA0;
+        need_jac = true;
+        status = ST_RUNNING;
+        fF = bsum(f * f, sm);
+        set_status_from(bmax(mag_bits(f), sm), A);
+        if (status == ST_RUNNING && A.maxiters <= 0) status = ST_MAXITERS;
+    }
+
+    NLS_DI void pass(const SolveArgs &A, SM &sm)
+    {
+        ++it;
+        if (need_jac) {
+            P a[R][R];
+            jacobian_tile(a, sm);
+            if (tid < n) sm.Fp[tid] = P(sm.F[tid]);
+            __syncthreads();
+            if (A.alg != ALG_NEWTON) {
+                // g = J^T F
+#pragma unroll
+                for (int bb = 0; bb < R; ++bb) {
+                    P s = P(0);
+#pragma unroll
+                    for (int aa = 0; aa < R; ++aa)
+                        if (row(aa) < n) s = fma(a[aa][bb], sm.Fp[row(aa)], s);
+                    if (col(bb) < CTA_NMAX) sm.red[ty][col(bb)] = s;
+                }
+                __syncthreads();
+                if (tid < n) {
+                    P s = P(0);
+#pragma unroll
+                    for (int q = 0; q < CTA_T; ++q) s += sm.red[q][tid];
+                    sm.g[tid] = s;
+                }
+                __syncthreads();
+                if (A.alg == ALG_TRUST_DOGLEG) {
+#pragma unroll
+                    for (int aa = 0; aa < R; ++aa) {
+                        P s = P(0);
+#pragma unroll
+                        for (int bb = 0; bb < R; ++bb)
+                            if (col(bb) < n) s = fma(a[aa][bb], sm.g[col(bb)], s);
+                        sm.red[tx][row(aa)] = s;
+                    }
+                    __syncthreads();
+                    if (tid < n) {
+                        P s = P(0);
+#pragma unroll
+                        for (int q = 0; q < CTA_T; ++q) s += sm.red[q][tid];
+                        sm.Jg[tid] = s;
+                    }
+                }
+            }
+            if (tid < n) sm.rhs[tid] = -sm.Fp[tid];
+            __syncthreads();
+            const bool ok = lu_solve(a, sm);
+            if (!ok) {
+                status = ST_SINGULAR;
+                return;
+            }
+            if (tid < n) sm.dN[tid] = double(sm.x[tid]);
+            __syncthreads();
+            need_jac = false;
+        }
+        const int t = tid;
+        const bool own = t < n;
+        if (A.alg == ALG_NEWTON) {
+            if (own) sm.u[t] += sm.dN[t];
+            __syncthreads();
+            const double f = residual_t(sm.u);
+            __syncthreads();
+            if (own) sm.F[t] = f;
+            ++nfev;
+            need_jac = true;
+            set_status_from(bmax(mag_bits(f), sm), A);
+        } else if (A.alg == ALG_NEWTON_BACKTRACK) {
+            const P s = bsum(own ? sm.g[t] * P(sm.dN[t]) : P(0), sm);
+            const double phi0 = 0.5 * fF;
+            double alpha = 1.0;
+            bool ok = false;
+            double f = 0.0, fFt = 0.0;
+            for (int m = 0; m < LS_MAX_TRIALS; ++m) {
+                if (own) sm.ut[t] = fma(alpha, sm.dN[t], sm.u[t]);
+                __syncthreads();
+                f = residual_t(sm.ut);
+                ++nfev;
+                fFt = bsum(f * f, sm);
+                const uint64_t mx = bmax(mag_bits(f), sm);
+                if (mx < INF64_BITS && 0.5 * fFt <= phi0 + LS_C1 * alpha * double(s)) {
+                    ok = true;
+                    if (own) {
+                        sm.u[t] = sm.ut[t];
+                        sm.F[t] = f;
+                    }
+                    fF = fFt;
+                    __syncthreads();
+                    set_status_from(mx, A);
+                    break;
+                }
+                alpha *= LS_RHO;
+            }
+            if (!ok) {
+                status = ST_LS_FAILED;
+                return;
+            }
+            need_jac = true;
+        } else {
+            const double dn = own ? sm.dN[t] : 0.0;
+            const P gt = own ? sm.g[t] : P(0), jgt = own ? sm.Jg[t] : P(0), fpt = own ? sm.Fp[t] : P(0);
+            const P D2 = P(Delta * Delta);
+            const P nN2 = bsum(P(dn) * P(dn), sm);
+            const P gg = bsum(gt * gt, sm);
+            const P JgJg = bsum(jgt * jgt, sm);
+            const P tt = gg / JgJg;
+            const P cc = tt * tt * gg;
+            const P w = P(dn) + tt * gt;
+            const P aa = bsum(w * w, sm);
+            const P bb = bsum(-tt * gt * w, sm);
+            double d;
+            P Jd;
+            if (nN2 <= D2) {
+                d = dn;
+                Jd = -fpt;
+            } else if (cc >= D2) {
+                const P sc = P(Delta) / nls_sqrt(gg);
+                d = double(-sc * gt);
+                Jd = -sc * jgt;
+            } else {
+                const P q = cc - D2;
+                const P tau = (-bb + nls_sqrt(bb * bb - aa * q)) / aa;
+                d = double(fma(tau, w, -tt * gt));
+                Jd = -(P(1) - tau) * tt * jgt - tau * fpt;
+            }
+            if (!own) {
+                d = 0.0;
+                Jd = P(0);
+            }
+            if (own) sm.ut[t] = sm.u[t] + d;
+            __syncthreads();
+            const double f = residual_t(sm.ut);
+            ++nfev;
+            const double fFt = bsum(f * f, sm);
+            const uint64_t mx = bmax(mag_bits(f), sm);
+            const P FJd = bsum(fpt * Jd, sm);
+            const P JdJd = bsum(Jd * Jd, sm);
+            const double pred = double(P(-2) * FJd - JdJd);
+            const double ared = fF - fFt;
+            if (pred > 0.0 && mx < INF64_BITS && ared > 0.0) {
+                if (own) {
+                    sm.u[t] = sm.ut[t];
+                    sm.F[t] = f;
+                }
+                fF = fFt;
+                need_jac = true;
+                rej = 0;
+                if (ared > TR_ETA_EXPAND * pred) Delta = fmin(TR_GROW * Delta, TR_DELTA_MAX);
+                __syncthreads();
+                set_status_from(mx, A);
+            } else {
+                Delta *= TR_SHRINK;
+                if (++rej >= TR_MAX_REJECTIONS) {
+                    status = ST_TR_STALLED;
+                    return;
+                }
+                if (it >= A.maxiters) status = ST_MAXITERS;
+            }
+        }
+    }
+
+    NLS_DI void finish(const SolveArgs &A, SM &sm) const
+    {
+        __syncthreads();
+        if (tid < n) A.u[(int64_t)tid * B + k] = sm.u[tid];
+        if (tid == 0) {
+            if (A.status) A.status[k] = status;
+            if (A.iters) A.iters[k] = it;
+            if (A.resid) A.resid[k] = bits_to_double(fmag);
+            if (A.nfev) A.nfev[k] = nfev;
+            if (A.solved && status == ST_SUCCESS) atomicAdd(A.solved, 1ull);
+        }
+    }
+};
+
+template <bool MIXED>
+constexpr int cta_smem_bytes()
+{
+    return (int)sizeof(CtaSmem<MIXED>);
+}
+
+template <int R, int FAM, bool MIXED>
+__global__ void __launch_bounds__(CTA_TPB) k_solve_cta(SolveArgs a)
+{
+    using S = CtaSolver<R, FAM, MIXED>;
+    using SM = CtaSmem<MIXED>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SM &sm = *reinterpret_cast<SM *>(smem_raw);
+    S s;
+    s.tid = threadIdx.x;
+    s.ty = s.tid / CTA_T;
+    s.tx = s.tid % CTA_T;
+    s.lane = s.tid & 31;
+    s.warp = s.tid >> 5;
+    s.n = a.n;
+    s.B = a.batch;
+    s.params = a.params;
+    bool first = true;
+    for (;;) {
+        if (s.tid == 0) {
+            long long next;
+            if (a.counter) next = (long long)atomicAdd(a.counter, 1ull);
+            else next = first ? (long long)blockIdx.x : (long long)a.batch;
+            sm.inst = next;
+        }
+        first = false;
+        __syncthreads();
+        s.k = sm.inst;
+        __syncthreads();
+        if (s.k >= a.batch) break;
+        s.init(a, sm);
+        while (s.status == ST_RUNNING) s.pass(a, sm);
+        s.finish(a, sm);
+    }
+}
+
+} // namespace nls

@@ -30,3 +30,9 @@ namespace nls {
 // or `lanes` when non-zero), runtime n <= L.
 KernelInfo warp_kernel(int family, int n, bool mixed, int lanes = 0);
 } // namespace nls
+
+namespace nls {
+// One instance per 256-thread CTA, register tiles of R x R (R = 4: n <= 64,
+// R = 8: n <= 128).
+KernelInfo cta_kernel(int family, int n, bool mixed);
+} // namespace nls

@@ -174,11 +174,18 @@ class Batch:
         return self.u0.shape[1]
 
 
+def cubic_g_sigma(n: int) -> float:
+    """Standard deviation of G: 0.3 up to n = 32 (all benchmark sizes); above
+    that 0.3 sqrt(32 / n), which keeps the spectral edge of sym(G) (about
+    0.42 sqrt(n) sigma / 0.3) below 3 so that sym(A) stays positive definite."""
+    return 0.3 if n <= 32 else 0.3 * math.sqrt(32.0 / n)
+
+
 def cubic_batch(n: int, B: int, seed: int = 0, config_id: int = 0,
                 b_half_width: float = 2.0, instances: np.ndarray | None = None) -> Batch:
     ids = np.arange(B, dtype=np.int64) if instances is None else np.asarray(instances)
     keys = stream_keys(seed, config_id, ids)
-    A, b, redraws = cubic_instances(keys, n, b_half_width)
+    A, b, redraws = cubic_instances(keys, n, b_half_width, g_sigma=cubic_g_sigma(n))
     K = ids.size
     params = np.empty((n * n + n, K))
     params[: n * n] = A.reshape(K, n * n).T
