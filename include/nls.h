@@ -116,8 +116,10 @@ int nls_batch_create(nls_handle *out, int device, void *cuda_stream, size_t mem_
  * returned iterate; out: optional per-instance outputs (NULL = none).
  * alg = nls_alg | nls_flags.  abstol >= 0 (finite), maxiters >= 0.
  * Requests are grouped until nls_flush or nls_status, which launch every
- * pending request of the handle together (one persistent launch for all
- * thread-tiled requests).  *req receives an id for nls_status.
+ * pending request of the handle together: each as a persistent kernel, all
+ * of them concurrently in one CUDA-graph launch, each with a share of the
+ * GPU proportional to its estimated work.  *req receives an id for
+ * nls_status.
  * batch == 0 is a no-op that still returns an id.
  * Errors: NLS_E_INVALID (null pointers, negative batch/maxiters, bad abstol,
  * unknown algorithm), NLS_E_UNSUPPORTED (n outside [1, 128], unknown family,
@@ -162,10 +164,31 @@ enum nls_option {
     NLS_OPT_REFILL_BELOW = 2, /* thread tiling, persistent: a warp refills its
                                  idle lanes when at most this many lanes are
                                  still iterating (0..31, default 24)           */
-    NLS_OPT_CTAS_PER_SM = 3   /* cap on resident CTAs per SM (0 = occupancy)   */
+    NLS_OPT_CTAS_PER_SM = 3,  /* cap on resident CTAs per SM (0 = occupancy)   */
+    NLS_OPT_GRAPH = 4         /* 1 (default): a flush is one CUDA-graph launch
+                                 (counter reset, one kernel node per request,
+                                 all concurrent, counter read-back), cached by
+                                 the shape of the group; 0: direct launches    */
 };
 /* Errors: NLS_E_INVALID for an unknown option or a value out of range. */
 int nls_set_option(nls_handle h, int option, int64_t value);
+
+/* Autotuner: times each tiling that can hold n (thread with refill
+ * thresholds 0/16/24/31 and warp with 8 lanes for n <= 8; warp with 16 or 32
+ * lanes for n <= 16 or 32; CTA for n > 8) on the first min(batch, 65536)
+ * instances of this batch, keeps the fastest for (family, n, algorithm,
+ * precision) in the handle's table, and restores u.  Later nls_solve calls
+ * without a tiling flag use the table, and its measured rate weights the
+ * share of the GPU each request of a flush gets.  Synchronous.  Same
+ * arguments as nls_solve (no tiling flag allowed); *chosen (may be NULL)
+ * receives the chosen NLS_TILE_* flag.  If the environment variable
+ * NLS_TUNE_CACHE names a file when a handle is created, the table is read
+ * from it. */
+int nls_autotune(nls_handle h, int family, const double *params, double *u, int n, int64_t batch,
+                 int alg, double abstol, int maxiters, int *chosen);
+/* Write / read the tuning table (text: family n alg tiles lanes refill rate). */
+int nls_tune_save(nls_handle h, const char *path);
+int nls_tune_load(nls_handle h, const char *path);
 
 /* ------------------------------------------------------------------------
  * Allocation-free solve (the paper has no counterpart).

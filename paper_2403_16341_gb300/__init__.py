@@ -37,11 +37,11 @@ NLS_TILE_CTA = 1 << 12
 NLS_OK, NLS_E_INVALID, NLS_E_CUDA, NLS_E_NOMEM = 0, -1, -2, -3
 NLS_E_UNSUPPORTED, NLS_E_TIMEOUT, NLS_E_BUSY, NLS_E_NOTFOUND = -4, -5, -6, -7
 # nls_option
-NLS_OPT_PERSISTENT, NLS_OPT_REFILL_BELOW, NLS_OPT_CTAS_PER_SM = 1, 2, 3
+NLS_OPT_PERSISTENT, NLS_OPT_REFILL_BELOW, NLS_OPT_CTAS_PER_SM, NLS_OPT_GRAPH = 1, 2, 3, 4
 
 EXPORTED = ("nls_batch_create", "nls_solve", "nls_flush", "nls_status", "nls_solve_host",
             "nls_batch_destroy", "nls_last_error", "nls_launch_count", "nls_set_option",
-            "nls_solve_noalloc")
+            "nls_solve_noalloc", "nls_autotune", "nls_tune_save", "nls_tune_load")
 NLS_NOALLOC_MAX_GROUPS = 64
 
 
@@ -92,6 +92,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "nls_set_option": ([vp, i32, i64], i32),
             "nls_solve_noalloc": ([vp, ctypes.POINTER(nls_group), i32, i32, dbl, i32,
                                    ctypes.POINTER(i64)], i32),
+            "nls_autotune": ([vp, i32, vp, vp, i32, i64, i32, dbl, i32,
+                              ctypes.POINTER(ctypes.c_int)], i32),
+            "nls_tune_save": ([vp, ctypes.c_char_p], i32),
+            "nls_tune_load": ([vp, ctypes.c_char_p], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -192,6 +196,22 @@ def nls_solve_noalloc(stream, groups, alg, abstol, maxiters, want_solved=True):
     return list(solved[:len(groups)]) if want_solved else None
 
 
+def nls_autotune(h, family, params, u, n, batch, alg, abstol, maxiters) -> int:
+    """Time the tilings that can hold n on this batch; returns the chosen NLS_TILE_* flag."""
+    chosen = ctypes.c_int(0)
+    _check(h, load_library().nls_autotune(h, family, params or None, u or None, n, batch, alg,
+                                          abstol, maxiters, ctypes.byref(chosen)))
+    return chosen.value
+
+
+def nls_tune_save(h, path: str) -> None:
+    _check(h, load_library().nls_tune_save(h, path.encode()))
+
+
+def nls_tune_load(h, path: str) -> None:
+    _check(h, load_library().nls_tune_load(h, path.encode()))
+
+
 # ------------------------------------------------------------- torch helpers
 
 class Solver:
@@ -236,6 +256,12 @@ class Solver:
 
     def flush(self) -> None:
         nls_flush(self.h)
+
+    def autotune(self, family: int, params, u, alg: int, abstol: float = 1e-10,
+                 maxiters: int = 50) -> int:
+        n, B = u.shape
+        p = params.data_ptr() if params is not None and params.numel() else 0
+        return nls_autotune(self.h, family, p, u.data_ptr(), n, B, alg, abstol, maxiters)
 
     def wait(self, req: int, timeout_ms: int = -1):
         return nls_status(self.h, req, timeout_ms)

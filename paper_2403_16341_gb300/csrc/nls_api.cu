@@ -3,12 +3,16 @@
 // file only validates, allocates library workspace and enqueues.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
 #include <map>
+#include <sstream>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -72,6 +76,8 @@ struct Request {
     int64_t id = 0;
     SolveArgs args{};
     KernelInfo kern{};
+    int family = 0, tiles = 0, lanes = 0, refill = -1;
+    double rate = 0.0;                     // tuned rate (0 = use the cost model)
     int slot = -1;                         // first of 2 ring entries (solved, work counter)
     std::shared_ptr<cudaEvent_t> done;     // recorded after the request's group
     bool launched = false;
@@ -82,7 +88,21 @@ struct Opts {
     int persistent = 1;     // persistent grid with a work counter
     int refill_below = 24;  // refill idle lanes when running lanes <= this
     int ctas_per_sm = 0;    // 0 = occupancy limit
+    int graph = 1;          // flush through a cached CUDA graph
 };
+
+// Autotuner result for one (family, n, algorithm, precision).
+struct Tuned {
+    int tiles = 0;      // NLS_TILE_THREAD / WARP / CTA
+    int lanes = 0;      // warp tiling: lanes per instance
+    int refill = -1;    // thread tiling: refill threshold (-1 = handle option)
+    double rate = 0.0;  // measured instances per second on the whole GPU
+};
+
+inline long long tune_key(int family, int n, int alg)
+{
+    return ((long long)family << 40) | ((long long)n << 24) | (long long)(alg & (NLS_ALG_MASK | NLS_MIXED));
+}
 
 } // namespace
 
@@ -105,6 +125,12 @@ struct nls_batch {
     // staging for nls_solve_host
     void *d_stage = nullptr;
     size_t stage_bytes = 0;
+    // cached executable graphs by request-shape signature
+    std::map<std::string, cudaGraphExec_t> graphs;
+    std::map<const void *, int> occ_cache;
+    std::map<long long, Tuned> tuned;
+    double *d_tune = nullptr; // autotuner scratch for a prefix of u
+    size_t tune_bytes = 0;
 };
 
 static std::mutex g_err_mu;
@@ -160,27 +186,70 @@ static int dev_alloc(nls_batch *h, void **p, size_t bytes)
     return NLS_OK;
 }
 
-// Pick the kernel for one request: a forced tiling flag, else thread (n <= 8),
-// warp (n <= 32) or CTA (n <= 128).
-static int select_kernel(nls_batch *h, int family, int n, int alg, KernelInfo *out)
+// Pick the kernel for one request: a forced tiling flag, else the autotuned
+// choice for (family, n, algorithm, precision), else thread (n <= 8), warp
+// (n <= 32) or CTA (n <= 128).
+static int select_kernel(nls_batch *h, int family, int n, int alg, KernelInfo *out, int *tiles_out,
+                         int *lanes_out, int *refill_out, double *rate_out)
 {
     const bool mixed = (alg & NLS_MIXED) != 0;
     const bool analytic = (alg & NLS_ANALYTIC_JAC) != 0;
     int tiles = alg & (NLS_TILE_THREAD | NLS_TILE_WARP | NLS_TILE_CTA);
+    int lanes = 0, refill = -1;
+    double rate = 0.0;
     if (tiles && (tiles & (tiles - 1)))
         return fail(h, NLS_E_INVALID, "more than one tiling flag in alg 0x%x", alg);
+    if (!tiles) {
+        auto it = h->tuned.find(tune_key(family, n, alg));
+        if (it != h->tuned.end()) {
+            tiles = it->second.tiles;
+            lanes = it->second.lanes;
+            refill = it->second.refill;
+            rate = it->second.rate;
+        }
+    }
     if (!tiles) tiles = n <= 8 ? NLS_TILE_THREAD : n <= 32 ? NLS_TILE_WARP : NLS_TILE_CTA;
     if (tiles == NLS_TILE_THREAD) {
         if (n > 8) return fail(h, NLS_E_UNSUPPORTED, "thread tiling holds n <= 8 (n = %d)", n);
         *out = thread_kernel(family, n, mixed, analytic);
     } else if (tiles == NLS_TILE_WARP) {
         if (n > 32) return fail(h, NLS_E_UNSUPPORTED, "warp tiling holds n <= 32 (n = %d)", n);
-        *out = warp_kernel(family, n, mixed, 0);
+        *out = warp_kernel(family, n, mixed, lanes);
     } else {
         *out = cta_kernel(family, n, mixed);
     }
     if (!out->launch) return fail(h, NLS_E_UNSUPPORTED, "no kernel for family %d, n = %d", family, n);
+    if (tiles_out) *tiles_out = tiles;
+    if (lanes_out) *lanes_out = lanes;
+    if (refill_out) *refill_out = refill;
+    if (rate_out) *rate_out = rate;
     return NLS_OK;
+}
+
+static int occupancy(nls_batch *h, const KernelInfo &k, int *occ)
+{
+    auto it = h->occ_cache.find(k.func);
+    if (it != h->occ_cache.end()) {
+        *occ = it->second;
+        return NLS_OK;
+    }
+    int o = 0;
+    NLS_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k.func, k.block, k.smem));
+    h->occ_cache[k.func] = o;
+    *occ = o;
+    return NLS_OK;
+}
+
+// Whole-GPU seconds a request needs: batch / tuned rate, else a cost model
+// (about six passes of an LU-dominated iteration; FP64 work weighs ~4x more).
+static double est_seconds(const Request &r)
+{
+    if (r.args.batch <= 0) return 0.0;
+    if (r.rate > 0.0) return double(r.args.batch) / r.rate;
+    const double n = r.args.n;
+    const double flops = 6.0 * (2.0 * n * n * n / 3.0 + 12.0 * n * n + 40.0 * n);
+    const double per_s = 2.5e11; // rough whole-GPU FP64-equivalent rate of these kernels
+    return double(r.args.batch) * flops / per_s;
 }
 
 static int wait_event(nls_batch *h, cudaEvent_t ev, int timeout_ms)
@@ -226,6 +295,130 @@ static int ring_take(nls_batch *h, int count, int *start)
     return NLS_OK;
 }
 
+// Launch geometry of every pending request.  Persistent grids share the GPU
+// in proportion to each request's estimated work, so that requests flushed
+// together (the buckets of an uneven batch) run side by side and finish
+// together; a lone request gets the full occupancy-limited grid.
+static int plan_grids(nls_batch *h, const std::vector<Request *> &rs, std::vector<int> &grids)
+{
+    double total = 0.0;
+    int live = 0;
+    for (Request *r : rs)
+        if (r->args.batch > 0) {
+            total += est_seconds(*r);
+            ++live;
+        }
+    grids.assign(rs.size(), 0);
+    for (size_t i = 0; i < rs.size(); ++i) {
+        Request &r = *rs[i];
+        if (r.args.batch == 0) continue;
+        const int64_t ctas = (r.args.batch + r.kern.per_cta - 1) / r.kern.per_cta;
+        if (!h->opt.persistent) {
+            grids[i] = (int)std::min<int64_t>(ctas, INT32_MAX);
+            r.args.counter = nullptr;
+            r.args.refill_below = 0;
+            continue;
+        }
+        int occ = 0;
+        int rc = occupancy(h, r.kern, &occ);
+        if (rc) return rc;
+        if (h->opt.ctas_per_sm > 0) occ = std::min(occ, h->opt.ctas_per_sm);
+        const int64_t full = (int64_t)std::max(occ, 1) * h->sms;
+        int64_t share = full;
+        if (live > 1 && total > 0.0) share = std::max<int64_t>(1, (int64_t)std::llround(full * est_seconds(r) / total));
+        grids[i] = (int)std::min(ctas, share);
+        r.args.counter = h->d_ctr + r.slot + 1;
+        r.args.refill_below = r.refill >= 0 ? r.refill : h->opt.refill_below;
+    }
+    return NLS_OK;
+}
+
+// Memset of the group's counters -> one kernel node per request (no edges
+// between them, so they run concurrently) -> copy of the counters to the
+// host.  The executable graph is cached by the shape of the group and
+// updated in place on later flushes of the same shape.
+static int launch_graph(nls_batch *h, const std::vector<Request *> &rs, const std::vector<int> &grids, int s0,
+                        int nctr)
+{
+    std::ostringstream sig;
+    cudaGraph_t g = nullptr;
+    NLS_CUDA(h, cudaGraphCreate(&g, 0));
+    struct Guard {
+        cudaGraph_t g;
+        ~Guard() { cudaGraphDestroy(g); }
+    } guard{g};
+    cudaMemsetParams mp{};
+    mp.dst = h->d_ctr + s0;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = (size_t)nctr * 2;
+    mp.height = 1;
+    cudaGraphNode_t ms = nullptr;
+    NLS_CUDA(h, cudaGraphAddMemsetNode(&ms, g, nullptr, 0, &mp));
+    std::vector<cudaGraphNode_t> kn;
+    int64_t launched = 0;
+    for (size_t i = 0; i < rs.size(); ++i) {
+        if (!grids[i]) continue;
+        Request &r = *rs[i];
+        void *kargs[] = {&r.args};
+        cudaKernelNodeParams kp{};
+        kp.func = const_cast<void *>(r.kern.func);
+        kp.gridDim = dim3(grids[i]);
+        kp.blockDim = dim3(r.kern.block);
+        kp.sharedMemBytes = r.kern.smem;
+        kp.kernelParams = kargs;
+        cudaGraphNode_t node = nullptr;
+        NLS_CUDA(h, cudaGraphAddKernelNode(&node, g, &ms, 1, &kp));
+        kn.push_back(node);
+        sig << r.kern.func << ':' << grids[i] << ';';
+        ++launched;
+    }
+    cudaGraphNode_t cp = nullptr;
+    NLS_CUDA(h, cudaGraphAddMemcpyNode1D(&cp, g, kn.empty() ? &ms : kn.data(), kn.empty() ? 1 : kn.size(),
+                                         h->h_ctr + s0, h->d_ctr + s0, sizeof(unsigned long long) * nctr,
+                                         cudaMemcpyDeviceToHost));
+    sig << '#' << nctr;
+    const std::string key = sig.str();
+    auto it = h->graphs.find(key);
+    cudaGraphExec_t exec = nullptr;
+    if (it != h->graphs.end()) {
+        cudaGraphExecUpdateResultInfo info{};
+        if (cudaGraphExecUpdate(it->second, g, &info) == cudaSuccess) {
+            exec = it->second;
+        } else {
+            cudaGetLastError();
+            cudaGraphExecDestroy(it->second);
+            h->graphs.erase(it);
+        }
+    }
+    if (!exec) {
+        if (h->graphs.size() >= 64) {
+            cudaGraphExecDestroy(h->graphs.begin()->second);
+            h->graphs.erase(h->graphs.begin());
+        }
+        NLS_CUDA(h, cudaGraphInstantiate(&exec, g, 0));
+        h->graphs[key] = exec;
+    }
+    NLS_CUDA(h, cudaGraphLaunch(exec, h->stream));
+    h->launches += launched;
+    return NLS_OK;
+}
+
+static int launch_direct(nls_batch *h, const std::vector<Request *> &rs, const std::vector<int> &grids, int s0,
+                         int nctr)
+{
+    NLS_CUDA(h, cudaMemsetAsync(h->d_ctr + s0, 0, sizeof(unsigned long long) * nctr, h->stream));
+    for (size_t i = 0; i < rs.size(); ++i) {
+        if (!grids[i]) continue;
+        cudaError_t e = rs[i]->kern.launch(rs[i]->args, grids[i], h->stream);
+        if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+        ++h->launches;
+    }
+    NLS_CUDA(h, cudaMemcpyAsync(h->h_ctr + s0, h->d_ctr + s0, sizeof(unsigned long long) * nctr,
+                                cudaMemcpyDeviceToHost, h->stream));
+    return NLS_OK;
+}
+
 static int flush_pending(nls_batch *h)
 {
     if (h->pending.empty()) return NLS_OK;
@@ -233,12 +426,12 @@ static int flush_pending(nls_batch *h)
     int s0 = 0;
     int rc = ring_take(h, 2 * nreq, &s0);
     if (rc) return rc;
-    NLS_CUDA(h, cudaMemsetAsync(h->d_ctr + s0, 0, sizeof(unsigned long long) * 2 * nreq, h->stream));
     auto ev = std::shared_ptr<cudaEvent_t>(new cudaEvent_t, [](cudaEvent_t *e) {
         cudaEventDestroy(*e);
         delete e;
     });
     NLS_CUDA(h, cudaEventCreateWithFlags(ev.get(), cudaEventDisableTiming));
+    std::vector<Request *> rs;
     for (int i = 0; i < nreq; ++i) {
         Request &r = h->reqs[h->pending[i]];
         r.slot = s0 + 2 * i;
@@ -246,28 +439,13 @@ static int flush_pending(nls_batch *h)
         r.args.solved = h->d_ctr + r.slot;
         r.done = ev;
         r.launched = true;
-        if (r.args.batch == 0) continue;
-        const int64_t ctas = (r.args.batch + r.kern.per_cta - 1) / r.kern.per_cta;
-        int grid = (int)std::min<int64_t>(ctas, INT32_MAX);
-        if (h->opt.persistent) {
-            int occ = 0;
-            NLS_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r.kern.func, r.kern.block,
-                                                                      r.kern.smem));
-            if (h->opt.ctas_per_sm > 0) occ = std::min(occ, h->opt.ctas_per_sm);
-            occ = std::max(occ, 1);
-            grid = (int)std::min<int64_t>(ctas, (int64_t)occ * h->sms);
-            r.args.counter = h->d_ctr + r.slot + 1;
-            r.args.refill_below = h->opt.refill_below;
-        } else {
-            r.args.counter = nullptr;
-            r.args.refill_below = 0;
-        }
-        cudaError_t e = r.kern.launch(r.args, grid, h->stream);
-        if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "kernel launch: %s", cudaGetErrorString(e));
-        ++h->launches;
+        rs.push_back(&r);
     }
-    NLS_CUDA(h, cudaMemcpyAsync(h->h_ctr + s0, h->d_ctr + s0, sizeof(unsigned long long) * 2 * nreq,
-                                cudaMemcpyDeviceToHost, h->stream));
+    std::vector<int> grids;
+    rc = plan_grids(h, rs, grids);
+    if (rc) return rc;
+    rc = h->opt.graph ? launch_graph(h, rs, grids, s0, 2 * nreq) : launch_direct(h, rs, grids, s0, 2 * nreq);
+    if (rc) return rc;
     NLS_CUDA(h, cudaEventRecord(*ev, h->stream));
     h->pending.clear();
     return NLS_OK;
@@ -288,6 +466,68 @@ static int validate(nls_batch *h, int family, const double *params, const double
         return fail(h, NLS_E_INVALID, "unknown flags in alg 0x%x", alg);
     if (batch > 0 && !u) return fail(h, NLS_E_INVALID, "u is NULL");
     if (batch > 0 && n_params(family, n) > 0 && !params) return fail(h, NLS_E_INVALID, "params is NULL");
+    return NLS_OK;
+}
+
+static int load_tuning(nls_batch *h, const char *path)
+{
+    std::ifstream f(path);
+    if (!f) return fail(h, NLS_E_INVALID, "cannot read tuning table %s", path);
+    std::string line;
+    int loaded = 0;
+    while (std::getline(f, line)) {
+        if (line.empty() || line[0] == '#') continue;
+        std::istringstream is(line);
+        int fam, n, alg;
+        Tuned t;
+        if (is >> fam >> n >> alg >> t.tiles >> t.lanes >> t.refill >> t.rate) {
+            h->tuned[tune_key(fam, n, alg)] = t;
+            ++loaded;
+        }
+    }
+    return loaded;
+}
+
+// One timed trial of a tiling on the first S instances of a request; u's
+// prefix is restored from `save` before the run.
+static int tune_trial(nls_batch *h, const SolveArgs &base, const KernelInfo &k, int refill, const double *save,
+                      int64_t S, unsigned long long *ctr, float *ms_out)
+{
+    SolveArgs a = base;
+    a.batch = S;
+    a.solved = ctr;
+    a.counter = ctr + 1;
+    a.refill_below = refill >= 0 ? refill : h->opt.refill_below;
+    a.status = nullptr;
+    a.iters = nullptr;
+    a.resid = nullptr;
+    a.nfev = nullptr;
+    int occ = 0;
+    int rc = occupancy(h, k, &occ);
+    if (rc) return rc;
+    const int64_t ctas = (S + k.per_cta - 1) / k.per_cta;
+    const int grid = (int)std::min<int64_t>(ctas, (int64_t)std::max(occ, 1) * h->sms);
+    cudaEvent_t e0, e1;
+    NLS_CUDA(h, cudaEventCreate(&e0));
+    NLS_CUDA(h, cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+        NLS_CUDA(h, cudaMemcpy2DAsync(base.u, base.ld * 8, save, S * 8, S * 8, base.n, cudaMemcpyDeviceToDevice,
+                                      h->stream));
+        NLS_CUDA(h, cudaMemsetAsync(ctr, 0, 16, h->stream));
+        NLS_CUDA(h, cudaEventRecord(e0, h->stream));
+        cudaError_t e = k.launch(a, grid, h->stream);
+        if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "tuning launch: %s", cudaGetErrorString(e));
+        ++h->launches;
+        NLS_CUDA(h, cudaEventRecord(e1, h->stream));
+        NLS_CUDA(h, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        NLS_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+        best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_out = best;
     return NLS_OK;
 }
 
@@ -316,6 +556,7 @@ int nls_batch_create(nls_handle *out, int device, void *cuda_stream, size_t mem_
         return fail(nullptr, NLS_E_CUDA, "cudaMallocHost: %s", cudaGetErrorString(e));
     }
     h->owner.assign(RING, 0);
+    if (const char *cache = std::getenv("NLS_TUNE_CACHE")) load_tuning(h.get(), cache);
     *out = h.release();
     return NLS_OK;
 }
@@ -327,12 +568,14 @@ int nls_solve(nls_handle h, int family, const double *params, double *u, int n, 
     if (rc) return rc;
     if (!req) return fail(h, NLS_E_INVALID, "req is NULL");
     Request r;
-    rc = select_kernel(h, family, n, alg, &r.kern);
+    rc = select_kernel(h, family, n, alg, &r.kern, &r.tiles, &r.lanes, &r.refill, &r.rate);
     if (rc) return rc;
+    r.family = family;
     r.id = h->next_id++;
     r.args.params = params;
     r.args.u = u;
     r.args.batch = batch;
+    r.args.ld = batch;
     r.args.n = n;
     r.args.alg = alg & NLS_ALG_MASK;
     r.args.abstol = abstol;
@@ -433,6 +676,8 @@ int nls_batch_destroy(nls_handle h)
     flush_pending(h);
     cudaStreamSynchronize(h->stream);
     h->reqs.clear();
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    if (h->d_tune) cudaFree(h->d_tune);
     if (h->d_stage) cudaFree(h->d_stage);
     if (h->d_ctr) cudaFree(h->d_ctr);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);
@@ -449,6 +694,100 @@ const char *nls_last_error(nls_handle h)
 
 int64_t nls_launch_count(nls_handle h) { return h ? h->launches : 0; }
 
+int nls_autotune(nls_handle h, int family, const double *params, double *u, int n, int64_t batch, int alg,
+                 double abstol, int maxiters, int *chosen)
+{
+    int rc = validate(h, family, params, u, n, batch, alg, abstol, maxiters);
+    if (rc) return rc;
+    if (alg & (NLS_TILE_THREAD | NLS_TILE_WARP | NLS_TILE_CTA))
+        return fail(h, NLS_E_INVALID, "nls_autotune chooses the tiling: pass no tiling flag");
+    NLS_CUDA(h, cudaSetDevice(h->device));
+    rc = flush_pending(h);
+    if (rc) return rc;
+    if (batch == 0) return NLS_OK;
+    const int64_t S = std::min<int64_t>(batch, 1 << 16);
+    const size_t need = (size_t)n * (size_t)S * 8 + 256;
+    if (need > h->tune_bytes) {
+        NLS_CUDA(h, cudaStreamSynchronize(h->stream));
+        if (h->d_tune) {
+            cudaFree(h->d_tune);
+            h->mem_used -= h->tune_bytes;
+            h->d_tune = nullptr;
+            h->tune_bytes = 0;
+        }
+        rc = dev_alloc(h, (void **)&h->d_tune, need);
+        if (rc) return rc;
+        h->tune_bytes = need;
+    }
+    double *save = h->d_tune;
+    auto *ctr = reinterpret_cast<unsigned long long *>(h->d_tune + (size_t)n * (size_t)S);
+    NLS_CUDA(h, cudaMemcpy2DAsync(save, S * 8, u, batch * 8, S * 8, n, cudaMemcpyDeviceToDevice, h->stream));
+    const bool mixed = (alg & NLS_MIXED) != 0, analytic = (alg & NLS_ANALYTIC_JAC) != 0;
+    std::vector<Tuned> cands;
+    auto add = [&](int tiles, int lanes, int refill) {
+        Tuned t;
+        t.tiles = tiles;
+        t.lanes = lanes;
+        t.refill = refill;
+        cands.push_back(t);
+    };
+    if (n <= 8) {
+        for (int r : {0, 16, 24, 31}) add(NLS_TILE_THREAD, 0, r);
+        add(NLS_TILE_WARP, 8, -1);
+    }
+    if (n <= 16) add(NLS_TILE_WARP, 16, -1);
+    if (n <= 32) add(NLS_TILE_WARP, 32, -1);
+    if (n > 8) add(NLS_TILE_CTA, 0, -1);
+    SolveArgs base{};
+    base.params = params;
+    base.u = u;
+    base.ld = batch;
+    base.n = n;
+    base.alg = alg & NLS_ALG_MASK;
+    base.abstol = abstol;
+    base.maxiters = maxiters;
+    Tuned best;
+    for (Tuned &c : cands) {
+        KernelInfo k = c.tiles == NLS_TILE_THREAD ? thread_kernel(family, n, mixed, analytic)
+                       : c.tiles == NLS_TILE_WARP ? warp_kernel(family, n, mixed, c.lanes)
+                                                  : cta_kernel(family, n, mixed);
+        if (!k.launch) continue;
+        float ms = 0.f;
+        rc = tune_trial(h, base, k, c.refill, save, S, ctr, &ms);
+        if (rc) return rc;
+        c.rate = double(S) / (double(ms) * 1e-3);
+        if (c.rate > best.rate) best = c;
+    }
+    NLS_CUDA(h, cudaMemcpy2DAsync(u, batch * 8, save, S * 8, S * 8, n, cudaMemcpyDeviceToDevice, h->stream));
+    NLS_CUDA(h, cudaStreamSynchronize(h->stream));
+    // the rate of a trial on S instances understates a full batch less than it
+    // matters here: it is only the relative weight of requests flushed together
+    h->tuned[tune_key(family, n, alg)] = best;
+    if (chosen) *chosen = best.tiles;
+    return NLS_OK;
+}
+
+int nls_tune_save(nls_handle h, const char *path)
+{
+    if (!h || !path) return NLS_E_INVALID;
+    std::ofstream f(path);
+    if (!f) return fail(h, NLS_E_INVALID, "cannot write tuning table %s", path);
+    f << "# family n alg tiles lanes refill rate\n";
+    for (auto &kv : h->tuned) {
+        const long long key = kv.first;
+        f << (key >> 40) << ' ' << ((key >> 24) & 0xffff) << ' ' << (key & 0xffffff) << ' ' << kv.second.tiles << ' '
+          << kv.second.lanes << ' ' << kv.second.refill << ' ' << kv.second.rate << '\n';
+    }
+    return f ? NLS_OK : fail(h, NLS_E_INVALID, "writing %s failed", path);
+}
+
+int nls_tune_load(nls_handle h, const char *path)
+{
+    if (!h || !path) return NLS_E_INVALID;
+    const int n = load_tuning(h, path);
+    return n < 0 ? n : NLS_OK;
+}
+
 int nls_set_option(nls_handle h, int option, int64_t value)
 {
     if (!h) return NLS_E_INVALID;
@@ -458,6 +797,7 @@ int nls_set_option(nls_handle h, int option, int64_t value)
         if (value < 0 || value > 31) return fail(h, NLS_E_INVALID, "refill threshold %lld outside [0, 31]", (long long)value);
         h->opt.refill_below = (int)value;
         return NLS_OK;
+    case NLS_OPT_GRAPH: h->opt.graph = value != 0; return NLS_OK;
     case NLS_OPT_CTAS_PER_SM:
         if (value < 0 || value > 64) return fail(h, NLS_E_INVALID, "CTAs per SM %lld outside [0, 64]", (long long)value);
         h->opt.ctas_per_sm = (int)value;

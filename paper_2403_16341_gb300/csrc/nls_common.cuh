@@ -36,9 +36,10 @@ constexpr int TR_MAX_REJECTIONS = 32;
 
 // Everything one launch needs for one uniform-size group of instances.
 struct SolveArgs {
-    const double *params; // [E][batch]
-    double *u;            // [n][batch], u0 in, iterate out
-    int64_t batch;
+    const double *params; // [E][ld]
+    double *u;            // [n][ld], u0 in, iterate out
+    int64_t batch;        // instances solved: k = 0 .. batch-1
+    int64_t ld;           // leading dimension (row stride) of params and u, >= batch
     int n;
     int alg;
     double abstol;

@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(CTA_TPB) k_solve_cta(SolveArgs a)
     s.lane = s.tid & 31;
     s.warp = s.tid >> 5;
     s.n = a.n;
-    s.B = a.batch;
+    s.B = a.ld;
     s.params = a.params;
     bool first = true;
     for (;;) {

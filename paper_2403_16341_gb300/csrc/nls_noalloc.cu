@@ -104,6 +104,7 @@ extern "C" int nls_solve_noalloc(void *cuda_stream, const nls_group *groups, int
         a.params = q.params;
         a.u = q.u;
         a.batch = q.batch;
+        a.ld = q.batch;
         a.n = q.n;
         a.alg = alg & NLS_ALG_MASK;
         a.abstol = abstol;

@@ -146,7 +146,7 @@ struct ThreadSolver {
     NLS_DI void init(const ParamView &pv, const SolveArgs &a, int64_t k)
     {
 #pragma unroll
-        for (int i = 0; i < N; ++i) u[i] = a.u[(int64_t)i * a.batch + k];
+        for (int i = 0; i < N; ++i) u[i] = a.u[(int64_t)i * a.ld + k];
         residual(pv, u, F);
         nfev = 1;
         it = 0;
@@ -164,7 +164,7 @@ struct ThreadSolver {
     NLS_DI void finish(const SolveArgs &a, int64_t k) const
     {
 #pragma unroll
-        for (int i = 0; i < N; ++i) a.u[(int64_t)i * a.batch + k] = u[i];
+        for (int i = 0; i < N; ++i) a.u[(int64_t)i * a.ld + k] = u[i];
         if (a.status) a.status[k] = status;
         if (a.iters) a.iters[k] = it;
         if (a.resid) a.resid[k] = bits_to_double(max_mag_bits(F));
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(THREAD_TPB) k_solve_thread(SolveArgs a)
                 k = cand;
 #pragma unroll 4
                 for (int e = 0; e < E; ++e) {
-                    const double v = __ldg(a.params + (int64_t)e * a.batch + k);
+                    const double v = __ldg(a.params + (int64_t)e * a.ld + k);
                     sd[e * THREAD_TPB + lane] = v;
                     if constexpr (MIXED) sf[e * THREAD_TPB + lane] = float(v);
                 }

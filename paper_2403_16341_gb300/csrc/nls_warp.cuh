@@ -254,7 +254,7 @@ struct WarpSolver {
     // Load instance k and test u0; executed by the lanes in `mask` (whole segments).
     NLS_DI void init(const SolveArgs &a, int64_t k, SM &sm, unsigned mask)
     {
-        const int64_t B = a.batch;
+        const int64_t B = a.ld;
         b_r = 0.0;
         if constexpr (FAM == FAM_CUBIC) {
 #pragma unroll
@@ -289,7 +289,7 @@ struct WarpSolver {
     // Write instance k's results (no cross-lane communication).
     NLS_DI void finish(const SolveArgs &a, int64_t k) const
     {
-        if (row_live()) a.u[(int64_t)r * a.batch + k] = u;
+        if (row_live()) a.u[(int64_t)r * a.ld + k] = u;
         if (r == 0) {
             if (a.status) a.status[k] = status;
             if (a.iters) a.iters[k] = it;
