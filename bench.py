@@ -236,6 +236,63 @@ def extras(args, nls, solver, batch, params, u0, stream, dev):
     return baseline, e2e
 
 
+def run_serving(args, nls, local, alg=LS | MIXED, rate=2000.0, warm_s=1.0, meas_s=5.0,
+                pool=512) -> dict:
+    """Open-loop serving run: Poisson arrivals at `rate` requests/s, each a
+    request of the config-3 mix (1-4096 instances, n in {3, 8, 16, 32},
+    cubic or Bratu), solved by the continuous-batching server.  Latency runs
+    from the scheduled arrival to the results being in host memory."""
+    import torch
+    payloads = I.serving_payloads(pool)
+    pinned = []
+    for b in payloads:
+        p = torch.from_numpy(np.ascontiguousarray(b.params)).pin_memory()
+        u = torch.zeros(b.u0.shape, dtype=torch.float64).pin_memory()
+        st = torch.zeros(b.batch, dtype=torch.int32).pin_memory()
+        pinned.append((p, u, st))
+    count = int(rate * (warm_s + meas_s))
+    arrivals = I.poisson_arrivals(count, rate)
+    srv = nls.nls_server_create(local, 0, 4)
+    tickets = [None] * count
+    last_use = {}
+    try:
+        t0 = nls.nls_server_now(srv) + 0.05
+        for i in range(count):
+            j = i % pool
+            if j in last_use:  # the payload's buffers are free again once its last use is done
+                prev = last_use.pop(j)
+                tickets[prev] = (tickets[prev][0], nls.nls_server_wait(srv, tickets[prev][0]))
+            b = payloads[j]
+            p, u, st = pinned[j]
+            u.zero_()
+            target = t0 + arrivals[i]
+            while nls.nls_server_now(srv) < target:
+                pass
+            tk = nls.nls_server_submit(srv, b.family, p.data_ptr() if p.numel() else 0,
+                                       u.data_ptr(), b.n, b.batch, alg, ABSTOL, MAXITERS,
+                                       st.data_ptr())
+            tickets[i] = (tk, None)
+            last_use[j] = i
+        for i in range(count):
+            if tickets[i][1] is None:
+                tickets[i] = (tickets[i][0], nls.nls_server_wait(srv, tickets[i][0]))
+        stats = nls.nls_server_stats(srv)
+    finally:
+        nls.nls_server_destroy(srv)
+    meas = [i for i in range(count) if arrivals[i] >= warm_s]
+    lat = np.array([tickets[i][1][2] - (t0 + arrivals[i]) for i in meas]) * 1e3
+    solved = sum(tickets[i][1][0] for i in meas)
+    asked = sum(payloads[i % pool].batch for i in meas)
+    span = max(tickets[i][1][2] for i in meas) - (t0 + arrivals[meas[0]])
+    return {"workload": "Poisson arrivals at 2000 req/s, 1-4096 instances per request "
+                        "(log-uniform), n in {3,8,16,32}, cubic or Bratu, NR+backtracking mixed",
+            "requests": len(meas), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "sustained_solved_per_s": solved / span, "offered_instances_per_s": asked / meas_s,
+            "solved_fraction": solved / asked, "max_queue": stats["max_queue"],
+            "max_inflight": stats["max_inflight"], "streams": 4}
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_2403_16341_gb300 as nls
@@ -332,6 +389,10 @@ def run_ours(args, world, rank, local):
     if not args.no_extras:
         baseline, e2e = extras(args, nls, solver, batch, params, u0, stream, dev)
 
+    serving = None
+    if not args.no_extras and not args.no_serving:
+        serving = run_serving(args, nls, local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -358,6 +419,7 @@ def run_ours(args, world, rank, local):
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                          "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+            "serving": serving,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),
         }
@@ -380,6 +442,7 @@ def main():
                     help="comma-separated subset of the step's variants (profiling runs)")
     ap.add_argument("--instances", type=int, default=B_FULL,
                     help="batch size (profiling runs; the benchmark uses 2^20)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-Newton bar, the end-to-end leg and the CPU baseline")
     args = ap.parse_args()

@@ -191,6 +191,46 @@ int nls_tune_save(nls_handle h, const char *path);
 int nls_tune_load(nls_handle h, const char *path);
 
 /* ------------------------------------------------------------------------
+ * Request server (continuous batching).
+ *
+ * Serves solve requests that arrive over time, each a batch of instances of
+ * one (family, n) on HOST buffers (pinned memory is fastest).  A dispatcher
+ * thread admits waiting requests in arrival order as soon as their device
+ * state fits in the server's arena (a block of device memory of
+ * mem_budget_bytes, 0 = half of the free memory; never more than free memory
+ * minus 1 GiB), copies their inputs in, and launches each wave of admitted
+ * requests through one of `streams` worker handles, so that waves admitted
+ * while others run overlap on the GPU.  Results (u and the per-instance
+ * outputs) are copied back into the caller's host buffers; then the arena
+ * space is released and waiting requests are admitted.  Each instance is
+ * solved exactly as by nls_solve with the same arguments.  The server is
+ * thread-safe: any thread may submit and wait. */
+typedef struct nls_server *nls_server_t;
+/* Errors: NLS_E_INVALID (streams outside 1..16), NLS_E_NOMEM, NLS_E_CUDA. */
+int nls_server_create(nls_server_t *out, int device, size_t mem_budget_bytes, int streams);
+/* Queue a request.  params / u / out are HOST pointers that must stay valid
+ * until nls_server_wait returns for the ticket; u holds u0 and receives the
+ * roots.  Same argument rules as nls_solve; NLS_E_NOMEM if the request can
+ * never fit in the arena. */
+int nls_server_submit(nls_server_t s, int family, const double *params, double *u, int n,
+                      int64_t batch, int alg, double abstol, int maxiters, const nls_outputs *out,
+                      int64_t *ticket);
+/* Wait (timeout_ms < 0: no limit) for a ticket; on NLS_OK its results are in
+ * the host buffers, *solved = #NLS_SUCCESS, *t_submit / *t_done = server
+ * clock (seconds, see nls_server_now) of submission and of the results
+ * being on the host.  The ticket is released. */
+int nls_server_wait(nls_server_t s, int64_t ticket, int64_t *solved, double *t_submit,
+                    double *t_done, int timeout_ms);
+/* Seconds since the server was created (monotonic clock). */
+double nls_server_now(nls_server_t s);
+/* Counters: admitted, completed, solved instances, max queue depth, max
+ * requests in flight, launch waves, queue depth, in flight, arena bytes,
+ * largest free arena block (the first ncounters of these). */
+int nls_server_stats(nls_server_t s, int64_t *counters, int ncounters);
+/* Finish all queued and in-flight work, then free the server. */
+int nls_server_destroy(nls_server_t s);
+
+/* ------------------------------------------------------------------------
  * Allocation-free solve (the paper has no counterpart).
  *
  * For callers that cannot allocate device memory: code running inside

@@ -41,7 +41,9 @@ NLS_OPT_PERSISTENT, NLS_OPT_REFILL_BELOW, NLS_OPT_CTAS_PER_SM, NLS_OPT_GRAPH = 1
 
 EXPORTED = ("nls_batch_create", "nls_solve", "nls_flush", "nls_status", "nls_solve_host",
             "nls_batch_destroy", "nls_last_error", "nls_launch_count", "nls_set_option",
-            "nls_solve_noalloc", "nls_autotune", "nls_tune_save", "nls_tune_load")
+            "nls_solve_noalloc", "nls_autotune", "nls_tune_save", "nls_tune_load",
+            "nls_server_create", "nls_server_submit", "nls_server_wait", "nls_server_now",
+            "nls_server_stats", "nls_server_destroy")
 NLS_NOALLOC_MAX_GROUPS = 64
 
 
@@ -96,6 +98,14 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                               ctypes.POINTER(ctypes.c_int)], i32),
             "nls_tune_save": ([vp, ctypes.c_char_p], i32),
             "nls_tune_load": ([vp, ctypes.c_char_p], i32),
+            "nls_server_create": ([ctypes.POINTER(vp), i32, ctypes.c_size_t, i32], i32),
+            "nls_server_submit": ([vp, i32, vp, vp, i32, i64, i32, dbl, i32, out_p,
+                                   ctypes.POINTER(i64)], i32),
+            "nls_server_wait": ([vp, i64, ctypes.POINTER(i64), ctypes.POINTER(dbl),
+                                 ctypes.POINTER(dbl), i32], i32),
+            "nls_server_now": ([vp], dbl),
+            "nls_server_stats": ([vp, ctypes.POINTER(i64), i32], i32),
+            "nls_server_destroy": ([vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -210,6 +220,56 @@ def nls_tune_save(h, path: str) -> None:
 
 def nls_tune_load(h, path: str) -> None:
     _check(h, load_library().nls_tune_load(h, path.encode()))
+
+
+def _gcheck(rc: int) -> None:
+    if rc:
+        raise NlsError(rc, load_library().nls_last_error(None).decode())
+
+
+def nls_server_create(device: int = 0, mem_budget_bytes: int = 0, streams: int = 4):
+    s = ctypes.c_void_p()
+    _gcheck(load_library().nls_server_create(ctypes.byref(s), device, mem_budget_bytes, streams))
+    return s.value
+
+
+def nls_server_submit(s, family, params, u, n, batch, alg, abstol, maxiters, status=0, iters=0,
+                      resid_inf=0, nfev=0) -> int:
+    """Queue a request on raw HOST addresses; returns its ticket."""
+    t = ctypes.c_int64()
+    out = _outs(status, iters, resid_inf, nfev)
+    _gcheck(load_library().nls_server_submit(s, family, params or None, u or None, n, batch, alg,
+                                             abstol, maxiters, ctypes.byref(out), ctypes.byref(t)))
+    return t.value
+
+
+def nls_server_wait(s, ticket: int, timeout_ms: int = -1):
+    """Returns (solved, t_submit, t_done) or None on NLS_E_TIMEOUT."""
+    sv, ts, td = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    rc = load_library().nls_server_wait(s, ticket, ctypes.byref(sv), ctypes.byref(ts),
+                                        ctypes.byref(td), timeout_ms)
+    if rc == NLS_E_TIMEOUT:
+        return None
+    _gcheck(rc)
+    return sv.value, ts.value, td.value
+
+
+def nls_server_now(s) -> float:
+    return load_library().nls_server_now(s)
+
+
+SERVER_COUNTERS = ("admitted", "completed", "solved", "max_queue", "max_inflight", "waves",
+                   "queued", "inflight", "arena_bytes", "largest_free")
+
+
+def nls_server_stats(s) -> dict:
+    c = (ctypes.c_int64 * len(SERVER_COUNTERS))()
+    _gcheck(load_library().nls_server_stats(s, c, len(SERVER_COUNTERS)))
+    return dict(zip(SERVER_COUNTERS, list(c)))
+
+
+def nls_server_destroy(s) -> None:
+    _gcheck(load_library().nls_server_destroy(s))
 
 
 # ------------------------------------------------------------- torch helpers

@@ -279,3 +279,44 @@ def workload_uneven(B: int = 1 << 18, seed: int = 0) -> list[Batch]:
 def workload_bratu_large(B: int = 16384, seed: int = 0) -> list[Batch]:
     """16,384 Bratu instances with n uniform in 64..128."""
     return bratu_uniform_n_batches(B, 64, 128, seed, config_id=4)
+
+
+# Serving workload -----------------------------------------------------------
+
+@dataclass
+class ServingRequest:
+    family: int
+    n: int
+    batch: int
+    params: np.ndarray  # [E, batch], float64, C-contiguous
+    arrival: float      # seconds after the start of the stream
+
+
+def serving_payloads(count: int, seed: int = 0, config_id: int = 3,
+                     max_batch: int = 4096) -> list[Batch]:
+    """`count` distinct request payloads: batch size floor(exp(U[0, ln(max_batch + 1))))
+    in 1..max_batch (log-uniform), n uniform in {3, 8, 16, 32}, family uniform
+    in {cubic (A = 3 I + G, b ~ U[-2, 2]^n), Bratu (lambda ~ U[0.5, 3])}, u0 = 0."""
+    keys = stream_keys(seed, config_id + 2000, np.arange(count))
+    u = uniforms(keys, 0, 3)
+    sizes = np.minimum(np.floor(np.exp(u[:, 0] * math.log(max_batch + 1))).astype(np.int64),
+                       max_batch)
+    sizes = np.maximum(sizes, 1)
+    ns = np.array([3, 8, 16, 32])[np.minimum((u[:, 1] * 4).astype(np.int64), 3)]
+    fams = (u[:, 2] < 0.5).astype(np.int64)  # 0 cubic, 1 Bratu
+    out, start = [], 0
+    for r in range(count):
+        ids = np.arange(start, start + sizes[r])
+        start += sizes[r]
+        if fams[r] == FAMILY_CUBIC:
+            out.append(cubic_batch(int(ns[r]), int(sizes[r]), seed, config_id, 2.0, instances=ids))
+        else:
+            out.append(bratu_batch(int(ns[r]), int(sizes[r]), seed, config_id, instances=ids))
+    return out
+
+
+def poisson_arrivals(count: int, rate: float, seed: int = 0, config_id: int = 3) -> np.ndarray:
+    """Arrival times (seconds) of a Poisson process with `rate` requests/s."""
+    keys = stream_keys(seed, config_id + 3000, np.arange(count))
+    gaps = -np.log1p(-uniforms(keys, 0, 1)[:, 0]) / rate
+    return np.cumsum(gaps)

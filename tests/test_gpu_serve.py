@@ -1,0 +1,102 @@
+"""Request server: continuous batching with admission by device memory.
+Every request's result equals the same request solved alone with nls_solve."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2403_16341_gb300 import inputs as I
+from tests.parity import gpu_solve
+
+pytestmark = pytest.mark.gpu
+
+LS, TR, MIXED = 1, 2, 1 << 8
+
+
+def run_stream(server, payloads, alg, gap_s=0.0):
+    import paper_2403_16341_gb300 as nls
+    bufs = []
+    for b in payloads:
+        p = np.ascontiguousarray(b.params)
+        u = np.ascontiguousarray(b.u0.copy())
+        st = np.zeros(b.batch, dtype=np.int32)
+        it = np.zeros(b.batch, dtype=np.int32)
+        bufs.append((p, u, st, it))
+    tickets = []
+
+    def producer():
+        for b, (p, u, st, it) in zip(payloads, bufs):
+            ptr = lambda a: a.ctypes.data if a.size else 0
+            tickets.append(nls.nls_server_submit(server, b.family, ptr(p), ptr(u), b.n, b.batch,
+                                                 alg, 1e-10, 50, ptr(st), ptr(it)))
+            if gap_s:
+                time.sleep(gap_s)
+
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    res = [nls.nls_server_wait(server, t) for t in tickets]
+    return bufs, res
+
+
+@pytest.mark.parametrize("alg", [LS | MIXED, TR])
+def test_mix_equals_alone(alg):
+    import paper_2403_16341_gb300 as nls
+    payloads = I.serving_payloads(120, max_batch=1024)
+    srv = nls.nls_server_create(0, 0, 4)
+    try:
+        bufs, res = run_stream(srv, payloads, alg, gap_s=0.0005)
+        stats = nls.nls_server_stats(srv)
+    finally:
+        nls.nls_server_destroy(srv)
+    solver = nls.Solver(0)
+    for b, (p, u, st, it), (solved, ts, td) in zip(payloads, bufs, res):
+        alone = gpu_solve(solver, b, alg)
+        np.testing.assert_array_equal(u, alone["u"])
+        np.testing.assert_array_equal(st, alone["status"])
+        np.testing.assert_array_equal(it, alone["iters"])
+        assert solved == alone["solved"] == b.batch
+        assert td >= ts
+    solver.close()
+    assert stats["completed"] == len(payloads) and stats["admitted"] == len(payloads)
+
+
+def test_small_arena_forces_queueing():
+    import paper_2403_16341_gb300 as nls
+    payloads = I.serving_payloads(60, max_batch=4096)
+    srv = nls.nls_server_create(0, 8 << 20, 2)  # 8 MiB of device state
+    try:
+        bufs, res = run_stream(srv, payloads, LS | MIXED)
+        stats = nls.nls_server_stats(srv)
+    finally:
+        nls.nls_server_destroy(srv)
+    assert stats["max_queue"] > 1
+    for b, (p, u, st, it), (solved, ts, td) in zip(payloads, bufs, res):
+        assert solved == b.batch and (st == 0).all()
+
+
+def test_oversize_request_rejected():
+    import paper_2403_16341_gb300 as nls
+    b = I.cubic_batch(32, 4096, config_id=3)
+    srv = nls.nls_server_create(0, 1 << 20, 1)
+    try:
+        u = b.u0.copy()
+        with pytest.raises(nls.NlsError) as e:
+            nls.nls_server_submit(srv, 0, b.params.ctypes.data, u.ctypes.data, 32, 4096, LS,
+                                  1e-10, 50)
+        assert e.value.code == nls.NLS_E_NOMEM
+    finally:
+        nls.nls_server_destroy(srv)
+
+
+def test_requests_overlap_on_the_device():
+    import paper_2403_16341_gb300 as nls
+    payloads = I.serving_payloads(200, max_batch=4096, seed=1)
+    srv = nls.nls_server_create(0, 0, 4)
+    try:
+        run_stream(srv, payloads, TR)
+        stats = nls.nls_server_stats(srv)
+    finally:
+        nls.nls_server_destroy(srv)
+    assert stats["max_inflight"] > 1 and stats["completed"] == 200
