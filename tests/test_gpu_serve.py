@@ -23,21 +23,31 @@ def run_stream(server, payloads, alg, gap_s=0.0):
         st = np.zeros(b.batch, dtype=np.int32)
         it = np.zeros(b.batch, dtype=np.int32)
         bufs.append((p, u, st, it))
-    tickets = []
+    tickets, errors = [], []
 
     def producer():
-        for b, (p, u, st, it) in zip(payloads, bufs):
-            ptr = lambda a: a.ctypes.data if a.size else 0
-            tickets.append(nls.nls_server_submit(server, b.family, ptr(p), ptr(u), b.n, b.batch,
-                                                 alg, 1e-10, 50, ptr(st), ptr(it)))
-            if gap_s:
-                time.sleep(gap_s)
+        try:
+            for b, (p, u, st, it) in zip(payloads, bufs):
+                ptr = lambda a: a.ctypes.data if a.size else 0
+                tickets.append(nls.nls_server_submit(server, b.family, ptr(p), ptr(u), b.n,
+                                                     b.batch, alg, 1e-10, 50, ptr(st), ptr(it)))
+                if gap_s:
+                    time.sleep(gap_s)
+        except Exception as e:  # surfaced in the test thread below
+            errors.append(e)
 
     th = threading.Thread(target=producer)
     th.start()
     th.join()
+    assert not errors, errors
+    assert len(tickets) == len(payloads)
     res = [nls.nls_server_wait(server, t) for t in tickets]
     return bufs, res
+
+
+def request_bytes(b):
+    al = lambda x: (x + 255) // 256 * 256
+    return al(b.params.size * 8) + al(b.u0.size * 8) + al(b.batch * 8) + 3 * al(b.batch * 4)
 
 
 @pytest.mark.parametrize("alg", [LS | MIXED, TR])
@@ -65,7 +75,9 @@ def test_mix_equals_alone(alg):
 def test_small_arena_forces_queueing():
     import paper_2403_16341_gb300 as nls
     payloads = I.serving_payloads(60, max_batch=4096)
-    srv = nls.nls_server_create(0, 8 << 20, 2)  # 8 MiB of device state
+    # room for the largest request and a little more: most requests must wait
+    budget = int(1.5 * max(request_bytes(b) for b in payloads))
+    srv = nls.nls_server_create(0, budget, 2)
     try:
         bufs, res = run_stream(srv, payloads, LS | MIXED)
         stats = nls.nls_server_stats(srv)
