@@ -79,61 +79,6 @@ NLS_DI uint64_t max_mag_bits(const double (&v)[N])
 
 NLS_DI double bits_to_double(uint64_t b) { return __longlong_as_double((long long)b); }
 
-// ---------------------------------------------------------------------------
-// FP64 <-> FP32 on the integer pipes, from the IEEE-754 binary64/binary32 bit
-// layouts, for the mixed-precision hand-offs (u and F into the FP32
-// Jacobian and right-hand side, the FP32 Newton step back to FP64).  GB300's
-// hardware conversions of 64-bit values share the scarce FP64 pipe.
-// narrow: sign and exponent exact, the 52-bit fraction truncated to 23 bits
-// (round toward zero, within one FP32 ulp); magnitudes below the FP32 normal
-// range give a signed zero, above it a signed infinity; NaN stays NaN.
-NLS_DI float narrow_rz(double x)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
-    const uint32_t sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7FFu);
-    const uint32_t frac = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-    uint32_t r;
-    if (e == 0x7FF) r = sign | 0x7F800000u | ((frac | (hi & 0xFFFFFu) | lo) ? 0x400000u : 0u);
-    else if (e > 1023 + 127) r = sign | 0x7F800000u;
-    else if (e < 1023 - 126) r = sign;
-    else r = sign | ((uint32_t)(e - 1023 + 127) << 23) | frac;
-    return __uint_as_float(r);
-}
-// widen: exact for normal numbers, infinities and NaN; FP32 subnormals give a signed zero.
-NLS_DI double widen(float f)
-{
-    const uint32_t b = __float_as_uint(f);
-    const uint32_t sign = b & 0x80000000u;
-    const uint32_t e = (b >> 23) & 0xFFu;
-    const uint32_t m = b & 0x7FFFFFu;
-    uint32_t hi, lo;
-    if (e == 0xFFu) {
-        hi = sign | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u);
-        lo = m << 29;
-    } else if (e == 0u) {
-        hi = sign;
-        lo = 0u;
-    } else {
-        hi = sign | ((e - 127u + 1023u) << 20) | (m >> 3);
-        lo = m << 29;
-    }
-    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
-}
-template <class P>
-NLS_DI P to_p(double x)
-{
-    if constexpr (std::is_same<P, double>::value) return x;
-    else return narrow_rz(x);
-}
-template <class P>
-NLS_DI double from_p(P x)
-{
-    if constexpr (std::is_same<P, double>::value) return x;
-    else return widen(x);
-}
-
 NLS_DI double rcp(double x) { return __drcp_rn(x); }
 NLS_DI float rcp(float x) { return __frcp_rn(x); }
 NLS_DI double nls_sqrt(double x) { return __dsqrt_rn(x); }

@@ -109,7 +109,7 @@ struct ThreadSolver {
     {
         P up[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) up[i] = to_p<P>(u[i]);
+        for (int i = 0; i < N; ++i) up[i] = P(u[i]);
         if constexpr (ANALYTIC) {
             Fm::template jac_analytic<P>(pv, up, J);
         } else {
@@ -138,7 +138,7 @@ struct ThreadSolver {
 
     // ------------------------------------------------------------ lane state
     double u[N], F[N], dN[N];
-    P g[N], Jg[N], Fp[N], dNp[N]; // dNp: the Newton step in the Jacobian precision
+    P g[N], Jg[N], Fp[N];
     double fF, Delta;
     int it, nfev, rej, status;
     bool need_jac;
@@ -179,7 +179,7 @@ struct ThreadSolver {
             P J[N][N], b[N];
             jacobian(pv, u, J);
 #pragma unroll
-            for (int i = 0; i < N; ++i) Fp[i] = to_p<P>(F[i]);
+            for (int i = 0; i < N; ++i) Fp[i] = P(F[i]);
             if (a.alg != ALG_NEWTON) {
                 // g = J^T F (gradient of 1/2 ||F||^2), taken before J is factored
 #pragma unroll
@@ -206,10 +206,7 @@ struct ThreadSolver {
                 return;
             }
 #pragma unroll
-            for (int i = 0; i < N; ++i) {
-                dNp[i] = b[i];
-                dN[i] = from_p<P>(b[i]);
-            }
+            for (int i = 0; i < N; ++i) dN[i] = double(b[i]);
             need_jac = false;
         }
 
@@ -223,7 +220,7 @@ struct ThreadSolver {
             // slope F^T J dN = g . dN (Eq. 9); phi(alpha) = 1/2 ||F(u + alpha dN)||^2
             P s = P(0);
 #pragma unroll
-            for (int i = 0; i < N; ++i) s = fma(g[i], dNp[i], s);
+            for (int i = 0; i < N; ++i) s = fma(g[i], P(dN[i]), s);
             const double phi0 = 0.5 * fF;
             double alpha = 1.0;
             bool ok = false;
@@ -234,7 +231,7 @@ struct ThreadSolver {
                 residual(pv, ut, Ft);
                 ++nfev;
                 const double fFt = sumsq(Ft);
-                if (max_mag_bits(Ft) < INF64_BITS && 0.5 * fFt <= phi0 + LS_C1 * alpha * from_p<P>(s)) {
+                if (max_mag_bits(Ft) < INF64_BITS && 0.5 * fFt <= phi0 + LS_C1 * alpha * double(s)) {
 #pragma unroll
                     for (int i = 0; i < N; ++i) { u[i] = ut[i]; F[i] = Ft[i]; }
                     fF = fFt;
@@ -253,10 +250,10 @@ struct ThreadSolver {
             // J d follows from linearity: J dN = -F, J c = -t J g (c = -t g).
             double d[N];
             P Jd[N];
-            const P D2 = to_p<P>(Delta * Delta);
+            const P D2 = P(Delta * Delta);
             P nN2 = P(0);
 #pragma unroll
-            for (int i = 0; i < N; ++i) nN2 = fma(dNp[i], dNp[i], nN2);
+            for (int i = 0; i < N; ++i) nN2 = fma(P(dN[i]), P(dN[i]), nN2);
             if (nN2 <= D2) {
 #pragma unroll
                 for (int i = 0; i < N; ++i) { d[i] = dN[i]; Jd[i] = -Fp[i]; }
@@ -267,14 +264,14 @@ struct ThreadSolver {
                 const P t = gg / JgJg; // Cauchy point c = -t g minimises m along -g
                 const P cc = t * t * gg;
                 if (cc >= D2) {
-                    const P sc = to_p<P>(Delta) / nls_sqrt(gg);
+                    const P sc = P(Delta) / nls_sqrt(gg);
 #pragma unroll
-                    for (int i = 0; i < N; ++i) { d[i] = from_p<P>(-sc * g[i]); Jd[i] = -sc * Jg[i]; }
+                    for (int i = 0; i < N; ++i) { d[i] = double(-sc * g[i]); Jd[i] = -sc * Jg[i]; }
                 } else {
                     P w[N], aa = P(0), bb = P(0);
 #pragma unroll
                     for (int i = 0; i < N; ++i) {
-                        w[i] = dNp[i] + t * g[i];
+                        w[i] = P(dN[i]) + t * g[i];
                         aa = fma(w[i], w[i], aa);
                         bb = fma(-t * g[i], w[i], bb);
                     }
@@ -282,7 +279,7 @@ struct ThreadSolver {
                     const P tau = (-bb + nls_sqrt(bb * bb - aa * q)) / aa;
 #pragma unroll
                     for (int i = 0; i < N; ++i) {
-                        d[i] = from_p<P>(fma(tau, w[i], -t * g[i]));
+                        d[i] = double(fma(tau, w[i], -t * g[i]));
                         Jd[i] = -(P(1) - tau) * t * Jg[i] - tau * Fp[i];
                     }
                 }
@@ -297,7 +294,7 @@ struct ThreadSolver {
             P FJd = P(0), JdJd = P(0);
 #pragma unroll
             for (int i = 0; i < N; ++i) { FJd = fma(Fp[i], Jd[i], FJd); JdJd = fma(Jd[i], Jd[i], JdJd); }
-            const double pred = from_p<P>(P(-2) * FJd - JdJd);
+            const double pred = double(P(-2) * FJd - JdJd);
             const double ared = fF - fFt;
             // pred > 0: rho > 0 <=> ared > 0, rho > eta <=> ared > eta pred (no FP64 divide)
             if (pred > 0.0 && max_mag_bits(Ft) < INF64_BITS && ared > 0.0) {
@@ -374,7 +371,7 @@ __global__ void __launch_bounds__(THREAD_TPB) k_solve_thread(SolveArgs a)
                 for (int e = 0; e < E; ++e) {
                     const double v = __ldg(a.params + (int64_t)e * a.ld + k);
                     sd[e * THREAD_TPB + lane] = v;
-                    if constexpr (MIXED) sf[e * THREAD_TPB + lane] = narrow_rz(v);
+                    if constexpr (MIXED) sf[e * THREAD_TPB + lane] = float(v);
                 }
                 s.init(pv, a, k);
                 got = true;
