@@ -429,6 +429,128 @@ def run_ours(args, world, rank, local):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- other workloads
+
+def _device_batches(torch, batches, dev):
+    out = []
+    for b in batches:
+        p = torch.from_numpy(np.ascontiguousarray(b.params)).to(dev) if b.params.size else None
+        u0 = torch.from_numpy(np.ascontiguousarray(b.u0)).to(dev)
+        outs = (torch.empty(b.batch, dtype=torch.int32, device=dev),
+                torch.empty(b.batch, dtype=torch.int32, device=dev),
+                torch.empty(b.batch, dtype=torch.float64, device=dev),
+                torch.empty(b.batch, dtype=torch.int32, device=dev))
+        out.append((b, p, u0, torch.empty_like(u0), outs))
+    return out
+
+
+def time_flush(torch, solver, dbs, alg, steps, warmup, stream):
+    """Solve every batch of `dbs` in one flush, `steps` times after `warmup`;
+    returns (median ms per flush, solved per flush, launches per flush)."""
+    times, solved, l0 = [], 0, None
+    for r in range(warmup + steps):
+        for _, _, u0, u, _ in dbs:
+            u.copy_(u0)
+        if r == warmup:
+            l0 = solver.launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reqs = [solver.submit(b.family, p, u, alg, ABSTOL, MAXITERS, outs)
+                for b, p, _, u, outs in dbs]
+        solver.flush()
+        e1.record(stream)
+        sv = sum(solver.wait(q) for q in reqs)
+        torch.cuda.synchronize()
+        if r >= warmup:
+            times.append(e0.elapsed_time(e1))
+            solved = sv
+    return float(np.median(times)), solved, (solver.launches() - l0) // steps
+
+
+def sampled_error(dbs, alg, per_batch=4, seed=0):
+    """Max relative error of the GPU roots against the polished FP64 oracle
+    on a sample of instances of every batch."""
+    import oracle as O
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    oalg = {0: O.ALG_NEWTON, 1: O.ALG_NEWTON_BACKTRACK, 2: O.ALG_TRUST_DOGLEG}[alg & 0xFF]
+    for b, _, _, u, _ in dbs:
+        idx = np.sort(rng.choice(b.batch, min(per_batch, b.batch), replace=False))
+        ug = u.cpu().numpy()[:, idx]
+        P = b.params[:, idx]
+        ou, st, *_ = O.solve_batch(b.family, P, b.u0[:, idx], oalg, ABSTOL, MAXITERS)
+        ref = O.polish_batch(b.family, P, ou)
+        err = np.abs(ug - ref).max(axis=0) / np.maximum(1.0, np.abs(ref).max(axis=0))
+        worst = max(worst, float(err.max()))
+    return worst
+
+
+def run_workload(args, local):
+    import torch
+    import paper_2403_16341_gb300 as nls
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    solver = nls.Solver(local, stream)
+    line = {"workload": args.workload, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "data": "synthetic", "unit": "solved systems/s", "results": {}}
+    res = line["results"]
+    if args.workload == "cubic3":
+        dbs = _device_batches(torch, [I.workload_cubic_n3()], dev)
+        line["config"] = "cubic n=3, 1024 instances, plain FP64 Newton, abstol 1e-10, maxiters 50"
+        for name, alg in (("analytic_jacobian", NEWTON | (1 << 9)), ("dual_jacobian", NEWTON)):
+            ms, sv, nl = time_flush(torch, solver, dbs, alg, args.steps, max(args.warmup, 3), stream)
+            res[name] = {"ms_per_batch": ms, "us_per_solve": 1e3 * ms / 1024,
+                         "solved_per_s": sv / (ms / 1e3), "solved": sv, "launches": nl,
+                         "max_rel_err": sampled_error(dbs, alg, 64)}
+    elif args.workload == "uneven":
+        batches = I.workload_uneven()
+        dbs = _device_batches(torch, batches, dev)
+        line["config"] = ("2^18 instances, n log-uniform in 2..32, half cubic half Bratu, "
+                          f"NR+backtracking, {len(batches)} (family, n) buckets in one flush")
+        for prec, m in (("fp64", 0), ("mixed", MIXED)):
+            alg = LS | m
+            for mode, persistent, graph in (("graph_concurrent", 1, 1), ("direct_serial", 1, 0),
+                                            ("static_serial", 0, 0)):
+                solver.set_option(nls.NLS_OPT_PERSISTENT, persistent)
+                solver.set_option(nls.NLS_OPT_GRAPH, graph)
+                ms, sv, nl = time_flush(torch, solver, dbs, alg, args.steps, max(args.warmup, 3),
+                                        stream)
+                res[f"{prec}_{mode}"] = {"ms": ms, "solved_per_s": sv / (ms / 1e3),
+                                         "solved": sv, "launches": nl}
+            solver.set_option(nls.NLS_OPT_PERSISTENT, 1)
+            solver.set_option(nls.NLS_OPT_GRAPH, 1)
+            # autotuned tiling per bucket, then the concurrent flush again
+            chosen = {}
+            for b, p, u0, u, _ in dbs:
+                u.copy_(u0)
+                chosen[f"{b.family}:{b.n}"] = solver.autotune(b.family, p, u, alg)
+            ms, sv, nl = time_flush(torch, solver, dbs, alg, args.steps, max(args.warmup, 3),
+                                    stream)
+            res[f"{prec}_graph_autotuned"] = {"ms": ms, "solved_per_s": sv / (ms / 1e3),
+                                              "solved": sv, "launches": nl,
+                                              "max_rel_err": sampled_error(dbs, alg, 2),
+                                              "tiles": {k: {1 << 10: "thread", 1 << 11: "warp",
+                                                            1 << 12: "cta"}[v]
+                                                        for k, v in chosen.items()}}
+            solver.close()
+            solver = nls.Solver(local, stream)  # fresh tuning table for the next precision
+    elif args.workload == "bratu-large":
+        batches = I.workload_bratu_large()
+        dbs = _device_batches(torch, batches, dev)
+        line["config"] = ("16,384 Bratu instances, n uniform in 64..128, lambda ~ U[0.5, 3], "
+                          "trust-region dogleg, one CTA per instance")
+        for name, alg in (("fp32_lu_fp64_residual", TR | MIXED), ("fp64_lu", TR)):
+            ms, sv, nl = time_flush(torch, solver, dbs, alg, args.steps, max(args.warmup, 3),
+                                    stream)
+            res[name] = {"ms": ms, "solved_per_s": sv / (ms / 1e3), "solved": sv,
+                         "launches": nl, "max_rel_err": sampled_error(dbs, alg, 1)}
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
+    solver.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -443,6 +565,9 @@ def main():
     ap.add_argument("--instances", type=int, default=B_FULL,
                     help="batch size (profiling runs; the benchmark uses 2^20)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--workload", default="cubic8",
+                    choices=["cubic8", "cubic3", "uneven", "bratu-large"],
+                    help="cubic8: the benchmark step; the others print their own JSON line")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-Newton bar, the end-to-end leg and the CPU baseline")
     args = ap.parse_args()
@@ -455,7 +580,9 @@ def main():
         VARIANTS[:] = [v for v in VARIANTS if v[0] in keep]
     if args.no_extras:
         args.no_cpu_baseline = True
-    if args.impl == "reference":
+    if args.workload != "cubic8":
+        run_workload(args, local)
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
         run_ours(args, world, rank, local)
