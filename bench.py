@@ -305,6 +305,8 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     solver = nls.Solver(local, stream)
+    if args.no_persistent:
+        solver.set_option(nls.NLS_OPT_PERSISTENT, 0)
 
     # every rank solves its own 2^20 instances (weak scaling, no exchange)
     batch = I.cubic_batch(N_SYS, args.instances, seed=rank, config_id=1, b_half_width=5.0)
@@ -565,6 +567,8 @@ def main():
     ap.add_argument("--instances", type=int, default=B_FULL,
                     help="batch size (profiling runs; the benchmark uses 2^20)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-persistent", action="store_true",
+                    help="one-block-per-chunk grids instead of persistent ones (comparison runs)")
     ap.add_argument("--workload", default="cubic8",
                     choices=["cubic8", "cubic3", "uneven", "bratu-large"],
                     help="cubic8: the benchmark step; the others print their own JSON line")

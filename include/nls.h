@@ -116,10 +116,10 @@ int nls_batch_create(nls_handle *out, int device, void *cuda_stream, size_t mem_
  * returned iterate; out: optional per-instance outputs (NULL = none).
  * alg = nls_alg | nls_flags.  abstol >= 0 (finite), maxiters >= 0.
  * Requests are grouped until nls_flush or nls_status, which launch every
- * pending request of the handle together: each as a persistent kernel, all
- * of them concurrently in one CUDA-graph launch, each with a share of the
- * GPU proportional to its estimated work.  *req receives an id for
- * nls_status.
+ * pending request of the handle together in one CUDA-graph launch: a lone
+ * request as a persistent kernel (work counter, idle lanes refilled), several
+ * requests as concurrent kernel nodes with full grids whose blocks the
+ * hardware interleaves.  *req receives an id for nls_status.
  * batch == 0 is a no-op that still returns an id.
  * Errors: NLS_E_INVALID (null pointers, negative batch/maxiters, bad abstol,
  * unknown algorithm), NLS_E_UNSUPPORTED (n outside [1, 128], unknown family,
@@ -178,8 +178,7 @@ int nls_set_option(nls_handle h, int option, int64_t value);
  * lanes for n <= 16 or 32; CTA for n > 8) on the first min(batch, 65536)
  * instances of this batch, keeps the fastest for (family, n, algorithm,
  * precision) in the handle's table, and restores u.  Later nls_solve calls
- * without a tiling flag use the table, and its measured rate weights the
- * share of the GPU each request of a flush gets.  Synchronous.  Same
+ * without a tiling flag use the table.  Synchronous.  Same
  * arguments as nls_solve (no tiling flag allowed); *chosen (may be NULL)
  * receives the chosen NLS_TILE_* flag.  If the environment variable
  * NLS_TUNE_CACHE names a file when a handle is created, the table is read

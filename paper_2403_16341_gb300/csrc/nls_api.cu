@@ -240,80 +240,26 @@ static int occupancy(nls_batch *h, const KernelInfo &k, int *occ)
     return NLS_OK;
 }
 
-// Whole-GPU seconds a request needs: batch / tuned rate, else a cost model
-// (about six passes of an LU-dominated iteration; FP64 work weighs ~4x more).
-static double est_seconds(const Request &r)
-{
-    if (r.args.batch <= 0) return 0.0;
-    if (r.rate > 0.0) return double(r.args.batch) / r.rate;
-    const double n = r.args.n;
-    const double flops = 6.0 * (2.0 * n * n * n / 3.0 + 12.0 * n * n + 40.0 * n);
-    const double per_s = 2.5e11; // rough whole-GPU FP64-equivalent rate of these kernels
-    return double(r.args.batch) * flops / per_s;
-}
-
-static int wait_event(nls_batch *h, cudaEvent_t ev, int timeout_ms)
-{
-    if (timeout_ms < 0) {
-        NLS_CUDA(h, cudaEventSynchronize(ev));
-        return NLS_OK;
-    }
-    auto t0 = std::chrono::steady_clock::now();
-    for (;;) {
-        cudaError_t e = cudaEventQuery(ev);
-        if (e == cudaSuccess) return NLS_OK;
-        if (e != cudaErrorNotReady) return fail(h, NLS_E_CUDA, "cudaEventQuery: %s", cudaGetErrorString(e));
-        auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0)
-                      .count();
-        if (ms >= timeout_ms) return fail(h, NLS_E_TIMEOUT, "request not complete after %d ms", timeout_ms);
-        std::this_thread::sleep_for(std::chrono::microseconds(50));
-    }
-}
-
-// Reserve `count` consecutive ring entries; requests still owning them are
-// waited for and their solved counts kept on the host first.
-static int ring_take(nls_batch *h, int count, int *start)
-{
-    if (count > RING) return fail(h, NLS_E_INVALID, "too many requests in one flush (%d)", count / 2);
-    if (h->ring_pos + count > RING) h->ring_pos = 0;
-    const int s = h->ring_pos;
-    for (int i = s; i < s + count; ++i) {
-        const int64_t id = h->owner[i];
-        if (!id) continue;
-        auto it = h->reqs.find(id);
-        if (it != h->reqs.end() && it->second.slot >= 0) {
-            Request &r = it->second;
-            NLS_CUDA(h, cudaEventSynchronize(*r.done));
-            r.solved_final = (long long)h->h_ctr[r.slot];
-            h->owner[r.slot] = h->owner[r.slot + 1] = 0;
-            r.slot = -1;
-        }
-        h->owner[i] = 0;
-    }
-    h->ring_pos = s + count;
-    *start = s;
-    return NLS_OK;
-}
-
-// Launch geometry of every pending request.  Persistent grids share the GPU
-// in proportion to each request's estimated work, so that requests flushed
-// together (the buckets of an uneven batch) run side by side and finish
-// together; a lone request gets the full occupancy-limited grid.
+// Launch geometry of every pending request.  A lone request runs as a
+// persistent grid (one wave of CTAs drawing instances from its work counter,
+// lanes refilled as instances finish).  When several requests are flushed
+// together (the buckets of an uneven batch, a serving wave), every kernel
+// gets its full one-block-per-chunk grid instead: the hardware interleaves
+// the CTAs of the concurrent graph nodes as they retire, which keeps the
+// GPU full without any cost model (a fixed split into small persistent
+// grids leaves SMs idle when only a few kernels run concurrently).
 static int plan_grids(nls_batch *h, const std::vector<Request *> &rs, std::vector<int> &grids)
 {
-    double total = 0.0;
     int live = 0;
     for (Request *r : rs)
-        if (r->args.batch > 0) {
-            total += est_seconds(*r);
-            ++live;
-        }
+        if (r->args.batch > 0) ++live;
+    const bool persistent = h->opt.persistent && live == 1;
     grids.assign(rs.size(), 0);
     for (size_t i = 0; i < rs.size(); ++i) {
         Request &r = *rs[i];
         if (r.args.batch == 0) continue;
         const int64_t ctas = (r.args.batch + r.kern.per_cta - 1) / r.kern.per_cta;
-        if (!h->opt.persistent) {
+        if (!persistent) {
             grids[i] = (int)std::min<int64_t>(ctas, INT32_MAX);
             r.args.counter = nullptr;
             r.args.refill_below = 0;
@@ -323,10 +269,7 @@ static int plan_grids(nls_batch *h, const std::vector<Request *> &rs, std::vecto
         int rc = occupancy(h, r.kern, &occ);
         if (rc) return rc;
         if (h->opt.ctas_per_sm > 0) occ = std::min(occ, h->opt.ctas_per_sm);
-        const int64_t full = (int64_t)std::max(occ, 1) * h->sms;
-        int64_t share = full;
-        if (live > 1 && total > 0.0) share = std::max<int64_t>(1, (int64_t)std::llround(full * est_seconds(r) / total));
-        grids[i] = (int)std::min(ctas, share);
+        grids[i] = (int)std::min<int64_t>(ctas, (int64_t)std::max(occ, 1) * h->sms);
         r.args.counter = h->d_ctr + r.slot + 1;
         r.args.refill_below = r.refill >= 0 ? r.refill : h->opt.refill_below;
     }
@@ -760,8 +703,6 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
     }
     NLS_CUDA(h, cudaMemcpy2DAsync(u, batch * 8, save, S * 8, S * 8, n, cudaMemcpyDeviceToDevice, h->stream));
     NLS_CUDA(h, cudaStreamSynchronize(h->stream));
-    // the rate of a trial on S instances understates a full batch less than it
-    // matters here: it is only the relative weight of requests flushed together
     h->tuned[tune_key(family, n, alg)] = best;
     if (chosen) *chosen = best.tiles;
     return NLS_OK;

@@ -142,6 +142,7 @@ struct ThreadSolver {
     double fF, Delta;
     int it, nfev, rej, status;
     bool need_jac;
+    bool have_g; // trust region: g = J^T F and J g formed for the current J
 
     NLS_DI void init(const ParamView &pv, const SolveArgs &a, int64_t k)
     {
@@ -153,6 +154,7 @@ struct ThreadSolver {
         rej = 0;
         Delta = TR_DELTA0;
         need_jac = true;
+        have_g = false;
         fF = sumsq(F);
         const uint64_t m = max_mag_bits(F);
         if (m >= INF64_BITS) status = ST_NONFINITE;
@@ -171,6 +173,27 @@ struct ThreadSolver {
         if (a.nfev) a.nfev[k] = nfev;
     }
 
+    // g = J^T Fp and, with jg, J g.
+    NLS_DI void gradient(const P (&J)[N][N], bool jg)
+    {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            P s = P(0);
+#pragma unroll
+            for (int i = 0; i < N; ++i) s = fma(J[i][j], Fp[i], s);
+            g[j] = s;
+        }
+        if (jg) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                P s = P(0);
+#pragma unroll
+                for (int j = 0; j < N; ++j) s = fma(J[i][j], g[j], s);
+                Jg[i] = s;
+            }
+        }
+    }
+
     // One loop pass (Jacobian use) of the chosen algorithm.
     NLS_DI void pass(const ParamView &pv, const SolveArgs &a)
     {
@@ -180,25 +203,10 @@ struct ThreadSolver {
             jacobian(pv, u, J);
 #pragma unroll
             for (int i = 0; i < N; ++i) Fp[i] = P(F[i]);
-            if (a.alg != ALG_NEWTON) {
-                // g = J^T F (gradient of 1/2 ||F||^2), taken before J is factored
-#pragma unroll
-                for (int j = 0; j < N; ++j) {
-                    P s = P(0);
-#pragma unroll
-                    for (int i = 0; i < N; ++i) s = fma(J[i][j], Fp[i], s);
-                    g[j] = s;
-                }
-                if (a.alg == ALG_TRUST_DOGLEG) {
-#pragma unroll
-                    for (int i = 0; i < N; ++i) {
-                        P s = P(0);
-#pragma unroll
-                        for (int j = 0; j < N; ++j) s = fma(J[i][j], g[j], s);
-                        Jg[i] = s;
-                    }
-                }
-            }
+            // g = J^T F (gradient of 1/2 ||F||^2), taken before J is factored; the
+            // trust region forms g and J g only when the Newton step leaves the region
+            if (a.alg == ALG_NEWTON_BACKTRACK) gradient(J, false);
+            have_g = false;
 #pragma unroll
             for (int i = 0; i < N; ++i) b[i] = -Fp[i];
             if (!lu_solve<N, P>(J, b)) {
@@ -258,6 +266,13 @@ struct ThreadSolver {
 #pragma unroll
                 for (int i = 0; i < N; ++i) { d[i] = dN[i]; Jd[i] = -Fp[i]; }
             } else {
+                if (!have_g) {
+                    // J at the same u again (the LU overwrote it): same values as before
+                    P J[N][N];
+                    jacobian(pv, u, J);
+                    gradient(J, true);
+                    have_g = true;
+                }
                 P gg = P(0), JgJg = P(0);
 #pragma unroll
                 for (int i = 0; i < N; ++i) { gg = fma(g[i], g[i], gg); JgJg = fma(Jg[i], Jg[i], JgJg); }
