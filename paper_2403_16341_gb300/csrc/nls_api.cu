@@ -240,6 +240,49 @@ static int occupancy(nls_batch *h, const KernelInfo &k, int *occ)
     return NLS_OK;
 }
 
+static int wait_event(nls_batch *h, cudaEvent_t ev, int timeout_ms)
+{
+    if (timeout_ms < 0) {
+        NLS_CUDA(h, cudaEventSynchronize(ev));
+        return NLS_OK;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return NLS_OK;
+        if (e != cudaErrorNotReady) return fail(h, NLS_E_CUDA, "cudaEventQuery: %s", cudaGetErrorString(e));
+        auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0)
+                      .count();
+        if (ms >= timeout_ms) return fail(h, NLS_E_TIMEOUT, "request not complete after %d ms", timeout_ms);
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+// Reserve `count` consecutive ring entries; requests still owning them are
+// waited for and their solved counts kept on the host first.
+static int ring_take(nls_batch *h, int count, int *start)
+{
+    if (count > RING) return fail(h, NLS_E_INVALID, "too many requests in one flush (%d)", count / 2);
+    if (h->ring_pos + count > RING) h->ring_pos = 0;
+    const int s = h->ring_pos;
+    for (int i = s; i < s + count; ++i) {
+        const int64_t id = h->owner[i];
+        if (!id) continue;
+        auto it = h->reqs.find(id);
+        if (it != h->reqs.end() && it->second.slot >= 0) {
+            Request &r = it->second;
+            NLS_CUDA(h, cudaEventSynchronize(*r.done));
+            r.solved_final = (long long)h->h_ctr[r.slot];
+            h->owner[r.slot] = h->owner[r.slot + 1] = 0;
+            r.slot = -1;
+        }
+        h->owner[i] = 0;
+    }
+    h->ring_pos = s + count;
+    *start = s;
+    return NLS_OK;
+}
+
 // Launch geometry of every pending request.  A lone request runs as a
 // persistent grid (one wave of CTAs drawing instances from its work counter,
 // lanes refilled as instances finish).  When several requests are flushed
