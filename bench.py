@@ -137,6 +137,22 @@ def dram_traffic(variant: str):
     return None
 
 
+def reduce_over_ranks(dist, ms: float, solved: int, device):
+    """Replicas: the job's time is the slowest rank's, its work the sum of all
+    ranks' solved instances (weak scaling, no data exchange)."""
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor([solved], device=device, dtype=torch.float64)
+    dist.all_reduce(s)
+    return float(t.item()), int(s.item())
+
+
+def shard_seed(rank: int) -> int:
+    """Each replica solves its own seeded batch."""
+    return rank
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -309,7 +325,7 @@ def run_ours(args, world, rank, local):
         solver.set_option(nls.NLS_OPT_PERSISTENT, 0)
 
     # every rank solves its own 2^20 instances (weak scaling, no exchange)
-    batch = I.cubic_batch(N_SYS, args.instances, seed=rank, config_id=1, b_half_width=5.0)
+    batch = I.cubic_batch(N_SYS, args.instances, seed=shard_seed(rank), config_id=1, b_half_width=5.0)
     params = torch.from_numpy(batch.params).to(dev)
     u0 = torch.from_numpy(batch.u0).to(dev)
     us = [torch.empty_like(u0) for _ in VARIANTS]
@@ -362,12 +378,7 @@ def run_ours(args, world, rank, local):
     launches = solver.launches() - l0
     ms_total = t0.elapsed_time(t1)
     if dist:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-        s = torch.tensor([solved_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(s)
-        solved_total = int(s.item())
+        ms_total, solved_total = reduce_over_ranks(dist, ms_total, solved_total, dev)
     ms_step = ms_total / args.steps
     value = solved_total / (ms_total / 1e3)
 
