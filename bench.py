@@ -351,6 +351,13 @@ def run_ours(args, world, rank, local):
     def finish(reqs):
         return [solver.wait(r) for r in reqs]
 
+    # the autotuner picks each variant's tiling and launch mode (untimed)
+    chosen = {}
+    if not args.no_autotune:
+        for i, (name, alg) in enumerate(VARIANTS):
+            us[i].copy_(u0)
+            t = solver.autotune(batch.family, params, us[i], alg, ABSTOL, MAXITERS)
+            chosen[name] = {1 << 10: "thread", 1 << 11: "warp", 1 << 12: "cta"}[t]
     for _ in range(max(args.warmup, 3)):
         finish(step())
     torch.cuda.synchronize()
@@ -391,6 +398,7 @@ def run_ours(args, world, rank, local):
         fl = algorithmic_fp64_flops(N_SYS, alg, it, nf)
         solved = int((st == 0).sum())
         variants[name] = {"ms": ms, "solved_per_s": solved / (ms / 1e3), "solved": solved,
+                          "tiling": chosen.get(name, "default"),
                           "mean_iters": float(it.mean()), "max_iters": int(it.max()),
                           "fp64_gflop": fl / 1e9, "fp64_tflops": fl / (ms / 1e3) / 1e12,
                           "max_resid": float(rs.max())}
@@ -578,6 +586,8 @@ def main():
     ap.add_argument("--instances", type=int, default=B_FULL,
                     help="batch size (profiling runs; the benchmark uses 2^20)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the default tiling instead of the autotuner's choice")
     ap.add_argument("--no-persistent", action="store_true",
                     help="one-block-per-chunk grids instead of persistent ones (comparison runs)")
     ap.add_argument("--workload", default="cubic8",

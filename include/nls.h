@@ -173,19 +173,23 @@ enum nls_option {
 /* Errors: NLS_E_INVALID for an unknown option or a value out of range. */
 int nls_set_option(nls_handle h, int option, int64_t value);
 
-/* Autotuner: times each tiling that can hold n (thread with refill
- * thresholds 0/16/24/31 and warp with 8 lanes for n <= 8; warp with 16 or 32
- * lanes for n <= 16 or 32; CTA for n > 8) on the first min(batch, 65536)
- * instances of this batch, keeps the fastest for (family, n, algorithm,
- * precision) in the handle's table, and restores u.  Later nls_solve calls
- * without a tiling flag use the table.  Synchronous.  Same
- * arguments as nls_solve (no tiling flag allowed); *chosen (may be NULL)
- * receives the chosen NLS_TILE_* flag.  If the environment variable
- * NLS_TUNE_CACHE names a file when a handle is created, the table is read
- * from it. */
+/* Autotuner: times each tiling that can hold n -- thread (n <= 8), warp with
+ * 8, 16 or 32 lanes (n <= lanes), CTA (n > 8) -- each both as a persistent
+ * grid (thread tiling: refill thresholds 0/16/24/31) and as a
+ * one-block-per-chunk grid, on the first min(batch, 65536) instances of this
+ * batch; keeps the fastest for (family, n, algorithm, precision) in the
+ * handle's table and restores u.  Later nls_solve calls without a tiling
+ * flag use the table (a request flushed alone takes the tuned launch mode;
+ * requests flushed together always use one-block-per-chunk grids).
+ * Synchronous.  Same arguments as nls_solve (no tiling flag allowed);
+ * *chosen (may be NULL) receives the chosen NLS_TILE_* flag.  If the
+ * environment variable NLS_TUNE_CACHE names a file when a handle is created,
+ * the table is read from it. */
 int nls_autotune(nls_handle h, int family, const double *params, double *u, int n, int64_t batch,
                  int alg, double abstol, int maxiters, int *chosen);
-/* Write / read the tuning table (text: family n alg tiles lanes refill rate). */
+/* Write / read the tuning table (text: family n alg tiles lanes refill rate;
+ * refill -2 = one-block-per-chunk grid, -1 = persistent with the handle's
+ * threshold, >= 0 = persistent with that threshold). */
 int nls_tune_save(nls_handle h, const char *path);
 int nls_tune_load(nls_handle h, const char *path);
 

@@ -95,9 +95,11 @@ struct Opts {
 struct Tuned {
     int tiles = 0;      // NLS_TILE_THREAD / WARP / CTA
     int lanes = 0;      // warp tiling: lanes per instance
-    int refill = -1;    // thread tiling: refill threshold (-1 = handle option)
+    int refill = -1;    // REFILL_STATIC: one-block-per-chunk grid; -1: persistent with the
+                        // handle's refill threshold; >= 0: persistent with this threshold
     double rate = 0.0;  // measured instances per second on the whole GPU
 };
+constexpr int REFILL_STATIC = -2;
 
 inline long long tune_key(int family, int n, int alg)
 {
@@ -296,12 +298,12 @@ static int plan_grids(nls_batch *h, const std::vector<Request *> &rs, std::vecto
     int live = 0;
     for (Request *r : rs)
         if (r->args.batch > 0) ++live;
-    const bool persistent = h->opt.persistent && live == 1;
     grids.assign(rs.size(), 0);
     for (size_t i = 0; i < rs.size(); ++i) {
         Request &r = *rs[i];
         if (r.args.batch == 0) continue;
         const int64_t ctas = (r.args.batch + r.kern.per_cta - 1) / r.kern.per_cta;
+        const bool persistent = h->opt.persistent && live == 1 && r.refill != REFILL_STATIC;
         if (!persistent) {
             grids[i] = (int)std::min<int64_t>(ctas, INT32_MAX);
             r.args.counter = nullptr;
@@ -482,8 +484,8 @@ static int tune_trial(nls_batch *h, const SolveArgs &base, const KernelInfo &k, 
     SolveArgs a = base;
     a.batch = S;
     a.solved = ctr;
-    a.counter = ctr + 1;
-    a.refill_below = refill >= 0 ? refill : h->opt.refill_below;
+    a.counter = refill == REFILL_STATIC ? nullptr : ctr + 1;
+    a.refill_below = refill >= 0 ? refill : refill == REFILL_STATIC ? 0 : h->opt.refill_below;
     a.status = nullptr;
     a.iters = nullptr;
     a.resid = nullptr;
@@ -492,7 +494,8 @@ static int tune_trial(nls_batch *h, const SolveArgs &base, const KernelInfo &k, 
     int rc = occupancy(h, k, &occ);
     if (rc) return rc;
     const int64_t ctas = (S + k.per_cta - 1) / k.per_cta;
-    const int grid = (int)std::min<int64_t>(ctas, (int64_t)std::max(occ, 1) * h->sms);
+    const int grid = refill == REFILL_STATIC ? (int)std::min<int64_t>(ctas, INT32_MAX)
+                                             : (int)std::min<int64_t>(ctas, (int64_t)std::max(occ, 1) * h->sms);
     cudaEvent_t e0, e1;
     NLS_CUDA(h, cudaEventCreate(&e0));
     NLS_CUDA(h, cudaEventCreate(&e1));
@@ -718,12 +721,14 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
         cands.push_back(t);
     };
     if (n <= 8) {
-        for (int r : {0, 16, 24, 31}) add(NLS_TILE_THREAD, 0, r);
-        add(NLS_TILE_WARP, 8, -1);
+        for (int r : {REFILL_STATIC, 0, 16, 24, 31}) add(NLS_TILE_THREAD, 0, r);
+        for (int r : {REFILL_STATIC, -1}) add(NLS_TILE_WARP, 8, r);
     }
-    if (n <= 16) add(NLS_TILE_WARP, 16, -1);
-    if (n <= 32) add(NLS_TILE_WARP, 32, -1);
-    if (n > 8) add(NLS_TILE_CTA, 0, -1);
+    for (int r : {REFILL_STATIC, -1}) {
+        if (n <= 16) add(NLS_TILE_WARP, 16, r);
+        if (n <= 32) add(NLS_TILE_WARP, 32, r);
+        if (n > 8) add(NLS_TILE_CTA, 0, r);
+    }
     SolveArgs base{};
     base.params = params;
     base.u = u;

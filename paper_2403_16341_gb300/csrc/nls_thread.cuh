@@ -138,7 +138,7 @@ struct ThreadSolver {
 
     // ------------------------------------------------------------ lane state
     double u[N], F[N], dN[N];
-    P g[N], Jg[N], Fp[N];
+    P g[N], Jg[N], Fp[N], dNp[N]; // dNp: the Newton step in the Jacobian precision
     double fF, Delta;
     int it, nfev, rej, status;
     bool need_jac;
@@ -214,7 +214,10 @@ struct ThreadSolver {
                 return;
             }
 #pragma unroll
-            for (int i = 0; i < N; ++i) dN[i] = double(b[i]);
+            for (int i = 0; i < N; ++i) {
+                dNp[i] = b[i];
+                dN[i] = double(b[i]);
+            }
             need_jac = false;
         }
 
@@ -228,7 +231,7 @@ struct ThreadSolver {
             // slope F^T J dN = g . dN (Eq. 9); phi(alpha) = 1/2 ||F(u + alpha dN)||^2
             P s = P(0);
 #pragma unroll
-            for (int i = 0; i < N; ++i) s = fma(g[i], P(dN[i]), s);
+            for (int i = 0; i < N; ++i) s = fma(g[i], dNp[i], s);
             const double phi0 = 0.5 * fF;
             double alpha = 1.0;
             bool ok = false;
@@ -261,7 +264,7 @@ struct ThreadSolver {
             const P D2 = P(Delta * Delta);
             P nN2 = P(0);
 #pragma unroll
-            for (int i = 0; i < N; ++i) nN2 = fma(P(dN[i]), P(dN[i]), nN2);
+            for (int i = 0; i < N; ++i) nN2 = fma(dNp[i], dNp[i], nN2);
             if (nN2 <= D2) {
 #pragma unroll
                 for (int i = 0; i < N; ++i) { d[i] = dN[i]; Jd[i] = -Fp[i]; }
@@ -286,7 +289,7 @@ struct ThreadSolver {
                     P w[N], aa = P(0), bb = P(0);
 #pragma unroll
                     for (int i = 0; i < N; ++i) {
-                        w[i] = P(dN[i]) + t * g[i];
+                        w[i] = dNp[i] + t * g[i];
                         aa = fma(w[i], w[i], aa);
                         bb = fma(-t * g[i], w[i], bb);
                     }
