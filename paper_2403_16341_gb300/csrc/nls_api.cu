@@ -358,7 +358,7 @@ static int launch_graph(nls_batch *h, const std::vector<Request *> &rs, const st
         cudaGraphNode_t node = nullptr;
         NLS_CUDA(h, cudaGraphAddKernelNode(&node, g, &ms, 1, &kp));
         kn.push_back(node);
-        sig << r.kern.func << ':' << grids[i] << ';';
+        sig << r.kern.func << ';'; // grids may differ: cudaGraphExecUpdate takes them
         ++launched;
     }
     cudaGraphNode_t cp = nullptr;
