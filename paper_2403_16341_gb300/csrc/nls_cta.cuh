@@ -47,11 +47,19 @@ struct CtaSmem {
     long long inst;
 };
 
+// Adds the factor U in pivot-position order, for the single-warp back
+// substitution (row stride NM + 1: a column walk hits 32 different banks).
+template <bool MIXED, int NM>
+struct CtaSmemU : CtaSmem<MIXED> {
+    typename CtaSmem<MIXED>::P U[NM][NM + 1];
+};
+
 template <int R, int FAM, bool MIXED>
 struct CtaSolver {
     using P = typename std::conditional<MIXED, float, double>::type;
     using K = decltype(mag_bits(P(0)));
-    using SM = CtaSmem<MIXED>;
+    static constexpr int NM = CTA_T * R;
+    using SM = CtaSmemU<MIXED, NM>;
 
     int tid, ty, tx, lane, warp, n;
     int64_t B, k;
@@ -174,7 +182,9 @@ struct CtaSolver {
 
     // ------------------------------------------------------------ LU
     // Solves J x = rhs (rhs in sm.rhs, x to sm.x); returns false on a zero or
-    // non-finite pivot (uniform over the CTA).
+    // non-finite pivot (uniform over the CTA).  The 16 owners of column k are
+    // one half-warp (tx = tid / 16), so the pivot candidates are reduced with
+    // shuffles; every thread then reads the single winner.
     NLS_DI bool lu_solve(P (&a)[R][R], SM &sm) const
     {
         const K inf = inf_bits(P(0));
@@ -188,7 +198,9 @@ struct CtaSolver {
                 const int kk = CTA_T * b + c;
                 if (kk >= n) break;
                 if (tx == c) {
-                    K best = 0;
+                    // local best over this thread's rows still at positions >= kk:
+                    // larger |a_ik| first, then the lower position
+                    uint64_t best = 0;
                     int bpos = INT_MAX, brow = -1;
                     P bval = P(0);
 #pragma unroll
@@ -197,7 +209,7 @@ struct CtaSolver {
                         if (i < n && mypos[aa] >= kk) {
                             K m = mag_bits(a[aa][b]);
                             if (mypos[aa] > kk && m > inf) m = K(0);
-                            if (brow < 0 || m > best || (m == best && mypos[aa] < bpos)) {
+                            if (brow < 0 || (uint64_t)m > best || ((uint64_t)m == best && mypos[aa] < bpos)) {
                                 best = m;
                                 bpos = mypos[aa];
                                 brow = i;
@@ -205,28 +217,28 @@ struct CtaSolver {
                             }
                         }
                     }
-                    sm.ckey[ty] = best;
-                    sm.cpos[ty] = bpos;
-                    sm.crow[ty] = brow;
-                    sm.cval[ty] = bval;
-                }
-                __syncthreads(); // S1
-                uint64_t best = 0;
-                int bpos = INT_MAX, prow_i = -1;
-                P pv = P(0);
+                    // half-warp butterfly: first the largest key, then the lowest position
+                    const unsigned hm = 0xFFFFu << (16 * (c & 1));
+                    uint64_t kmax = brow >= 0 ? best + 1 : 0; // +1: a valid zero key beats no candidate
 #pragma unroll
-                for (int q = 0; q < CTA_T; ++q) {
-                    const int cr = sm.crow[q];
-                    if (cr < 0) continue;
-                    const uint64_t ck = sm.ckey[q];
-                    const int cp = sm.cpos[q];
-                    if (prow_i < 0 || ck > best || (ck == best && cp < bpos)) {
-                        best = ck;
-                        bpos = cp;
-                        prow_i = cr;
-                        pv = sm.cval[q];
+                    for (int o = 8; o > 0; o >>= 1) {
+                        const uint64_t w = __shfl_xor_sync(hm, kmax, o);
+                        kmax = w > kmax ? w : kmax;
+                    }
+                    int pmin = (brow >= 0 && best + 1 == kmax) ? bpos : INT_MAX;
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1) pmin = min(pmin, __shfl_xor_sync(hm, pmin, o));
+                    if (brow >= 0 && bpos == pmin) {
+                        sm.ckey[0] = best;
+                        sm.cpos[0] = bpos;
+                        sm.crow[0] = brow;
+                        sm.cval[0] = bval;
                     }
                 }
+                __syncthreads(); // S1
+                const uint64_t best = sm.ckey[0];
+                const int bpos = sm.cpos[0], prow_i = sm.crow[0];
+                const P pv = sm.cval[0];
                 if (best == 0 || best >= (uint64_t)inf) ok = false;
                 const P r = rcp(pv);
                 bool rem[R];
@@ -264,34 +276,44 @@ struct CtaSolver {
                         if (bb > b || tx > c) a[aa][bb] -= l * sm.prow[col(bb)];
                     }
                 }
-                if (tid < n && tid != prow_i) {
-                    // rows still to be pivoted have lcol != 0 only where needed
-                    sm.rhs[tid] -= sm.lcol[tid] * sm.rhs[prow_i];
-                }
+                if (tid < n && tid != prow_i) sm.rhs[tid] -= sm.lcol[tid] * sm.rhs[prow_i];
                 // the next S1 orders these reads before lcol / prow are rewritten
             }
         }
+        // U in pivot-position order for the back substitution
+#pragma unroll
+        for (int aa = 0; aa < R; ++aa) {
+            if (row(aa) >= n) continue;
+#pragma unroll
+            for (int bb = 0; bb < R; ++bb)
+                if (col(bb) < n) sm.U[mypos[aa]][col(bb)] = a[aa][bb];
+        }
         __syncthreads();
-        // back substitution over positions n-1 .. 0
+        // back substitution by warp 0: lane l keeps the right-hand sides of
+        // positions l, l + 32, ...; one shuffle broadcasts x_k per step
+        if (warp == 0) {
+            constexpr int J = (NM + 31) / 32;
+            P y[J];
 #pragma unroll
-        for (int b = R - 1; b >= 0; --b) {
-            for (int c = CTA_T - 1; c >= 0; --c) {
-                const int kk = CTA_T * b + c;
-                if (kk >= n) continue;
-                if (tid == 0) {
-                    const int p = sm.pos_row[kk];
-                    sm.x[kk] = sm.rhs[p] * sm.rdiag[kk];
-                }
-                __syncthreads();
-                const P xk = sm.x[kk];
-                if (tx == c) {
+            for (int j = 0; j < J; ++j) {
+                const int p = lane + 32 * j;
+                y[j] = p < n ? sm.rhs[sm.pos_row[p]] : P(0);
+            }
+            for (int kk = n - 1; kk >= 0; --kk) {
+                const int jk = kk >> 5;
+                P yk = P(0);
 #pragma unroll
-                    for (int aa = 0; aa < R; ++aa)
-                        if (row(aa) < n && mypos[aa] < kk) sm.rhs[row(aa)] -= a[aa][b] * xk;
+                for (int j = 0; j < J; ++j) yk = (j == jk) ? y[j] : yk;
+                const P xk = __shfl_sync(0xffffffffu, yk * sm.rdiag[kk], kk & 31);
+                if (lane == 0) sm.x[kk] = xk;
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const int p = lane + 32 * j;
+                    if (p < kk) y[j] -= sm.U[p][kk] * xk;
                 }
-                __syncthreads();
             }
         }
+        __syncthreads();
         return ok;
     }
 
@@ -496,23 +518,23 @@ struct CtaSolver {
     }
 };
 
-template <bool MIXED>
+template <bool MIXED, int R>
 constexpr int cta_smem_bytes()
 {
-    return (int)sizeof(CtaSmem<MIXED>);
+    return (int)sizeof(CtaSmemU<MIXED, CTA_T * R>);
 }
 
 template <int R, int FAM, bool MIXED>
 __global__ void __launch_bounds__(CTA_TPB) k_solve_cta(SolveArgs a)
 {
     using S = CtaSolver<R, FAM, MIXED>;
-    using SM = CtaSmem<MIXED>;
+    using SM = typename S::SM;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SM &sm = *reinterpret_cast<SM *>(smem_raw);
     S s;
     s.tid = threadIdx.x;
-    s.ty = s.tid / CTA_T;
-    s.tx = s.tid % CTA_T;
+    s.tx = s.tid / CTA_T; // the 16 owners of a column form one half-warp
+    s.ty = s.tid % CTA_T;
     s.lane = s.tid & 31;
     s.warp = s.tid >> 5;
     s.n = a.n;

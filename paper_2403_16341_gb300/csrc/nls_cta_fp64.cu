@@ -7,18 +7,23 @@ namespace nls {
 template <int R, int FAM>
 static cudaError_t launch_cta_fp64(const SolveArgs &a, int grid, cudaStream_t st)
 {
-    k_solve_cta<R, FAM, false><<<grid, CTA_TPB, cta_smem_bytes<false>(), st>>>(a);
+    k_solve_cta<R, FAM, false><<<grid, CTA_TPB, cta_smem_bytes<false, R>(), st>>>(a);
     return cudaGetLastError();
 }
 
 template <int R, int FAM>
 static KernelInfo info_cta_fp64()
 {
+    // more than 48 KB of dynamic shared memory needs an opt-in, once per kernel
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        reinterpret_cast<const void *>(&k_solve_cta<R, FAM, false>),
+        cudaFuncAttributeMaxDynamicSharedMemorySize, cta_smem_bytes<false, R>());
+    (void)attr;
     KernelInfo k;
     k.launch = &launch_cta_fp64<R, FAM>;
     k.func = reinterpret_cast<const void *>(&k_solve_cta<R, FAM, false>);
     k.block = CTA_TPB;
-    k.smem = cta_smem_bytes<false>();
+    k.smem = cta_smem_bytes<false, R>();
     k.per_cta = 1;
     return k;
 }

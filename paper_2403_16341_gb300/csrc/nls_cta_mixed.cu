@@ -7,18 +7,23 @@ namespace nls {
 template <int R, int FAM>
 static cudaError_t launch_cta_mixed(const SolveArgs &a, int grid, cudaStream_t st)
 {
-    k_solve_cta<R, FAM, true><<<grid, CTA_TPB, cta_smem_bytes<true>(), st>>>(a);
+    k_solve_cta<R, FAM, true><<<grid, CTA_TPB, cta_smem_bytes<true, R>(), st>>>(a);
     return cudaGetLastError();
 }
 
 template <int R, int FAM>
 static KernelInfo info_cta_mixed()
 {
+    // more than 48 KB of dynamic shared memory needs an opt-in, once per kernel
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        reinterpret_cast<const void *>(&k_solve_cta<R, FAM, true>),
+        cudaFuncAttributeMaxDynamicSharedMemorySize, cta_smem_bytes<true, R>());
+    (void)attr;
     KernelInfo k;
     k.launch = &launch_cta_mixed<R, FAM>;
     k.func = reinterpret_cast<const void *>(&k_solve_cta<R, FAM, true>);
     k.block = CTA_TPB;
-    k.smem = cta_smem_bytes<true>();
+    k.smem = cta_smem_bytes<true, R>();
     k.per_cta = 1;
     return k;
 }
