@@ -39,6 +39,7 @@ struct CtaSmem {
     P rdiag[CTA_NMAX], x[CTA_NMAX];
     P red[CTA_T][CTA_NMAX]; // partial sums of J^T F and J g
     int pos_row[CTA_NMAX];  // row holding pivot position k
+    int row_pos[CTA_NMAX];  // position of row i after the interchanges so far
     uint64_t ckey[CTA_T];
     int cpos[CTA_T], crow[CTA_T];
     P cval[CTA_T];
@@ -188,9 +189,15 @@ struct CtaSolver {
     NLS_DI bool lu_solve(P (&a)[R][R], SM &sm) const
     {
         const K inf = inf_bits(P(0));
-        int mypos[R];
+        // bit aa: row(aa) exists and is not a pivot row yet
+        uint32_t remmask = 0;
 #pragma unroll
-        for (int aa = 0; aa < R; ++aa) mypos[aa] = row(aa);
+        for (int aa = 0; aa < R; ++aa) remmask |= (row(aa) < n ? 1u : 0u) << aa;
+        if (tid < n) {
+            sm.row_pos[tid] = tid; // position of row tid
+            sm.pos_row[tid] = tid; // row at position tid
+        }
+        __syncthreads();
         bool ok = true;
 #pragma unroll
         for (int b = 0; b < R; ++b) {
@@ -198,23 +205,23 @@ struct CtaSolver {
                 const int kk = CTA_T * b + c;
                 if (kk >= n) break;
                 if (tx == c) {
-                    // local best over this thread's rows still at positions >= kk:
-                    // larger |a_ik| first, then the lower position
+                    // local best over this thread's remaining rows: larger |a_ik|
+                    // first, then the lower position
                     uint64_t best = 0;
                     int bpos = INT_MAX, brow = -1;
                     P bval = P(0);
 #pragma unroll
                     for (int aa = 0; aa < R; ++aa) {
+                        if (!((remmask >> aa) & 1u)) continue;
                         const int i = row(aa);
-                        if (i < n && mypos[aa] >= kk) {
-                            K m = mag_bits(a[aa][b]);
-                            if (mypos[aa] > kk && m > inf) m = K(0);
-                            if (brow < 0 || (uint64_t)m > best || ((uint64_t)m == best && mypos[aa] < bpos)) {
-                                best = m;
-                                bpos = mypos[aa];
-                                brow = i;
-                                bval = a[aa][b];
-                            }
+                        const int pi = sm.row_pos[i];
+                        K m = mag_bits(a[aa][b]);
+                        if (pi > kk && m > inf) m = K(0);
+                        if (brow < 0 || (uint64_t)m > best || ((uint64_t)m == best && pi < bpos)) {
+                            best = m;
+                            bpos = pi;
+                            brow = i;
+                            bval = a[aa][b];
                         }
                     }
                     // half-warp butterfly: first the largest key, then the lowest position
@@ -241,35 +248,43 @@ struct CtaSolver {
                 const P pv = sm.cval[0];
                 if (best == 0 || best >= (uint64_t)inf) ok = false;
                 const P r = rcp(pv);
-                bool rem[R];
+                const bool mine = ty == (prow_i & (CTA_T - 1));
+                const int ap = prow_i / CTA_T;
+                const uint32_t rem = remmask & ~(mine ? 1u << ap : 0u);
+                if (tx == c) {
 #pragma unroll
-                for (int aa = 0; aa < R; ++aa) {
-                    rem[aa] = row(aa) < n && mypos[aa] >= kk && row(aa) != prow_i;
-                    if (tx == c && row(aa) < n) sm.lcol[row(aa)] = rem[aa] ? a[aa][b] * r : P(0);
+                    for (int aa = 0; aa < R; ++aa)
+                        if (row(aa) < n) sm.lcol[row(aa)] = ((rem >> aa) & 1u) ? a[aa][b] * r : P(0);
                 }
-                if (ty == (prow_i & (CTA_T - 1))) {
-                    const int ap = prow_i / CTA_T;
-#pragma unroll
-                    for (int bb = b; bb < R; ++bb) {
-                        P v = P(0);
-#pragma unroll
-                        for (int aa = 0; aa < R; ++aa) v = (aa == ap) ? a[aa][bb] : v;
-                        sm.prow[col(bb)] = v;
+                if (mine) {
+                    // the pivot row's slot is a runtime index: one case runs
+                    switch (ap) {
+#define NLS_PROW_CASE(A)                                                                          \
+    case A:                                                                                       \
+        if (A < R) {                                                                              \
+            _Pragma("unroll") for (int bb = b; bb < R; ++bb) sm.prow[col(bb)] = a[A < R ? A : 0][bb]; \
+        }                                                                                         \
+        break;
+                        NLS_PROW_CASE(0) NLS_PROW_CASE(1) NLS_PROW_CASE(2) NLS_PROW_CASE(3)
+                        NLS_PROW_CASE(4) NLS_PROW_CASE(5) NLS_PROW_CASE(6) NLS_PROW_CASE(7)
+#undef NLS_PROW_CASE
                     }
                 }
                 if (tid == 0) {
+                    // interchange: the pivot row takes position kk, the row that
+                    // held kk takes the pivot's old position
+                    const int q = sm.pos_row[kk];
+                    sm.row_pos[q] = bpos;
+                    sm.pos_row[bpos] = q;
+                    sm.row_pos[prow_i] = kk;
                     sm.pos_row[kk] = prow_i;
                     sm.rdiag[kk] = r;
                 }
-#pragma unroll
-                for (int aa = 0; aa < R; ++aa) {
-                    if (row(aa) == prow_i) mypos[aa] = kk;
-                    else if (mypos[aa] == kk) mypos[aa] = bpos;
-                }
                 __syncthreads(); // S2
+                remmask = rem;
 #pragma unroll
                 for (int aa = 0; aa < R; ++aa) {
-                    if (!rem[aa]) continue;
+                    if (!((rem >> aa) & 1u)) continue;
                     const P l = sm.lcol[row(aa)];
 #pragma unroll
                     for (int bb = b; bb < R; ++bb) {
@@ -277,16 +292,18 @@ struct CtaSolver {
                     }
                 }
                 if (tid < n && tid != prow_i) sm.rhs[tid] -= sm.lcol[tid] * sm.rhs[prow_i];
-                // the next S1 orders these reads before lcol / prow are rewritten
+                // the next S1 orders these reads before lcol / prow / row_pos are rewritten
             }
         }
+        __syncthreads();
         // U in pivot-position order for the back substitution
 #pragma unroll
         for (int aa = 0; aa < R; ++aa) {
             if (row(aa) >= n) continue;
+            const int pa = sm.row_pos[row(aa)];
 #pragma unroll
             for (int bb = 0; bb < R; ++bb)
-                if (col(bb) < n) sm.U[mypos[aa]][col(bb)] = a[aa][bb];
+                if (col(bb) < n) sm.U[pa][col(bb)] = a[aa][bb];
         }
         __syncthreads();
         // back substitution by warp 0: lane l keeps the right-hand sides of
