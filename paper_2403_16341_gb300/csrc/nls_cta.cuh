@@ -35,14 +35,14 @@ template <bool MIXED>
 struct CtaSmem {
     using P = typename std::conditional<MIXED, float, double>::type;
     double u[CTA_NMAX], F[CTA_NMAX], dN[CTA_NMAX], ut[CTA_NMAX], Ft[CTA_NMAX];
-    P Fp[CTA_NMAX], g[CTA_NMAX], Jg[CTA_NMAX], rhs[CTA_NMAX], lcol[CTA_NMAX], prow[CTA_NMAX];
+    P Fp[CTA_NMAX], g[CTA_NMAX], Jg[CTA_NMAX], rhs[CTA_NMAX];
+    P lcol[2][CTA_NMAX];    // multipliers of step k in buffer k & 1
     P rdiag[CTA_NMAX], x[CTA_NMAX];
     P red[CTA_T][CTA_NMAX]; // partial sums of J^T F and J g
     int pos_row[CTA_NMAX];  // row holding pivot position k
     int row_pos[CTA_NMAX];  // position of row i after the interchanges so far
-    uint64_t ckey[CTA_T];
-    int cpos[CTA_T], crow[CTA_T];
-    P cval[CTA_T];
+    uint64_t ckey[2];       // pivot of step k in slot k & 1: key, position, row
+    int cpos[2], crow[2];
     double rd[CTA_TPB / 32];
     uint64_t rm[CTA_TPB / 32];
     long long inst;
@@ -204,9 +204,10 @@ struct CtaSolver {
             for (int c = 0; c < CTA_T; ++c) {
                 const int kk = CTA_T * b + c;
                 if (kk >= n) break;
+                const int par = kk & 1;
                 if (tx == c) {
-                    // local best over this thread's remaining rows: larger |a_ik|
-                    // first, then the lower position
+                    // the owners of column kk: local best over their remaining rows
+                    // (larger |a_ik| first, then the lower position) ...
                     uint64_t best = 0;
                     int bpos = INT_MAX, brow = -1;
                     P bval = P(0);
@@ -224,7 +225,7 @@ struct CtaSolver {
                             bval = a[aa][b];
                         }
                     }
-                    // half-warp butterfly: first the largest key, then the lowest position
+                    // ... reduced over the half-warp ...
                     const unsigned hm = 0xFFFFu << (16 * (c & 1));
                     uint64_t kmax = brow >= 0 ? best + 1 : 0; // +1: a valid zero key beats no candidate
 #pragma unroll
@@ -235,64 +236,68 @@ struct CtaSolver {
                     int pmin = (brow >= 0 && best + 1 == kmax) ? bpos : INT_MAX;
 #pragma unroll
                     for (int o = 8; o > 0; o >>= 1) pmin = min(pmin, __shfl_xor_sync(hm, pmin, o));
-                    if (brow >= 0 && bpos == pmin) {
-                        sm.ckey[0] = best;
-                        sm.cpos[0] = bpos;
-                        sm.crow[0] = brow;
-                        sm.cval[0] = bval;
+                    const unsigned wb = __ballot_sync(hm, brow >= 0 && bpos == pmin);
+                    const int src = wb ? __ffs(wb) - 1 : (16 * (c & 1));
+                    const P pv = __shfl_sync(hm, bval, src);
+                    const int prow_i = __shfl_sync(hm, brow, src);
+                    const P r = rcp(pv);
+                    // ... which then write the multipliers of their rows and the pivot
+#pragma unroll
+                    for (int aa = 0; aa < R; ++aa) {
+                        const int i = row(aa);
+                        if (i < n) sm.lcol[par][i] = (((remmask >> aa) & 1u) && i != prow_i) ? a[aa][b] * r : P(0);
+                    }
+                    if (lane == src) {
+                        sm.ckey[par] = kmax ? kmax - 1 : 0;
+                        sm.cpos[par] = pmin;
+                        sm.crow[par] = prow_i;
+                        sm.rdiag[kk] = r;
+                        // interchange: the pivot row takes position kk, the row that
+                        // held kk takes the pivot's old position
+                        const int q = sm.pos_row[kk];
+                        sm.row_pos[q] = pmin;
+                        sm.pos_row[pmin] = q;
+                        sm.row_pos[prow_i] = kk;
+                        sm.pos_row[kk] = prow_i;
                     }
                 }
-                __syncthreads(); // S1
-                const uint64_t best = sm.ckey[0];
-                const int bpos = sm.cpos[0], prow_i = sm.crow[0];
-                const P pv = sm.cval[0];
+                __syncthreads(); // the one barrier of the step
+                const uint64_t best = sm.ckey[par];
+                const int prow_i = sm.crow[par];
                 if (best == 0 || best >= (uint64_t)inf) ok = false;
-                const P r = rcp(pv);
-                const bool mine = ty == (prow_i & (CTA_T - 1));
-                const int ap = prow_i / CTA_T;
-                const uint32_t rem = remmask & ~(mine ? 1u << ap : 0u);
-                if (tx == c) {
+                const int tp = prow_i & (CTA_T - 1); // ty of the pivot row's owners
+                const int ap = prow_i / CTA_T;       // ... and its slot in their tiles
+                const uint32_t rem = remmask & ~(ty == tp ? 1u << ap : 0u);
+                // the pivot row's entries of this thread's columns sit in lane tp of
+                // its half-warp (same tx): width-16 shuffles, slot chosen by a
+                // CTA-uniform switch
+                P pr[R];
 #pragma unroll
-                    for (int aa = 0; aa < R; ++aa)
-                        if (row(aa) < n) sm.lcol[row(aa)] = ((rem >> aa) & 1u) ? a[aa][b] * r : P(0);
-                }
-                if (mine) {
-                    // the pivot row's slot is a runtime index: one case runs
-                    switch (ap) {
+                for (int bb = 0; bb < R; ++bb) pr[bb] = P(0);
+                switch (ap) {
 #define NLS_PROW_CASE(A)                                                                          \
     case A:                                                                                       \
         if (A < R) {                                                                              \
-            _Pragma("unroll") for (int bb = b; bb < R; ++bb) sm.prow[col(bb)] = a[A < R ? A : 0][bb]; \
+            _Pragma("unroll") for (int bb = b; bb < R; ++bb) pr[bb] =                             \
+                __shfl_sync(0xffffffffu, a[A < R ? A : 0][bb], tp, CTA_T);                        \
         }                                                                                         \
         break;
-                        NLS_PROW_CASE(0) NLS_PROW_CASE(1) NLS_PROW_CASE(2) NLS_PROW_CASE(3)
-                        NLS_PROW_CASE(4) NLS_PROW_CASE(5) NLS_PROW_CASE(6) NLS_PROW_CASE(7)
+                    NLS_PROW_CASE(0) NLS_PROW_CASE(1) NLS_PROW_CASE(2) NLS_PROW_CASE(3)
+                    NLS_PROW_CASE(4) NLS_PROW_CASE(5) NLS_PROW_CASE(6) NLS_PROW_CASE(7)
 #undef NLS_PROW_CASE
-                    }
                 }
-                if (tid == 0) {
-                    // interchange: the pivot row takes position kk, the row that
-                    // held kk takes the pivot's old position
-                    const int q = sm.pos_row[kk];
-                    sm.row_pos[q] = bpos;
-                    sm.pos_row[bpos] = q;
-                    sm.row_pos[prow_i] = kk;
-                    sm.pos_row[kk] = prow_i;
-                    sm.rdiag[kk] = r;
-                }
-                __syncthreads(); // S2
                 remmask = rem;
 #pragma unroll
                 for (int aa = 0; aa < R; ++aa) {
                     if (!((rem >> aa) & 1u)) continue;
-                    const P l = sm.lcol[row(aa)];
+                    const P l = sm.lcol[par][row(aa)];
 #pragma unroll
                     for (int bb = b; bb < R; ++bb) {
-                        if (bb > b || tx > c) a[aa][bb] -= l * sm.prow[col(bb)];
+                        if (bb > b || tx > c) a[aa][bb] -= l * pr[bb];
                     }
                 }
-                if (tid < n && tid != prow_i) sm.rhs[tid] -= sm.lcol[tid] * sm.rhs[prow_i];
-                // the next S1 orders these reads before lcol / prow / row_pos are rewritten
+                if (tid < n && tid != prow_i) sm.rhs[tid] -= sm.lcol[par][tid] * sm.rhs[prow_i];
+                // the next barrier orders these reads before buffer `par` is reused
             }
         }
         __syncthreads();
