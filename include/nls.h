@@ -193,11 +193,6 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
 int nls_tune_save(nls_handle h, const char *path);
 int nls_tune_load(nls_handle h, const char *path);
 
-/* Diagnostic: y[i] = the device reciprocal the FP64 LU uses for its pivots
- * (x, y DEVICE float64[n]; asynchronous on cuda_stream).  Not part of any
- * solve; it lets tests bound that reciprocal's error. */
-int nls_probe_rcp(const double *x, double *y, int64_t n, void *cuda_stream);
-
 /* ------------------------------------------------------------------------
  * Request server (continuous batching).
  *

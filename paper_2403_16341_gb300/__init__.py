@@ -43,7 +43,7 @@ EXPORTED = ("nls_batch_create", "nls_solve", "nls_flush", "nls_status", "nls_sol
             "nls_batch_destroy", "nls_last_error", "nls_launch_count", "nls_set_option",
             "nls_solve_noalloc", "nls_autotune", "nls_tune_save", "nls_tune_load",
             "nls_server_create", "nls_server_submit", "nls_server_wait", "nls_server_now",
-            "nls_server_stats", "nls_server_destroy", "nls_probe_rcp")
+            "nls_server_stats", "nls_server_destroy")
 NLS_NOALLOC_MAX_GROUPS = 64
 
 
@@ -106,7 +106,6 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "nls_server_now": ([vp], dbl),
             "nls_server_stats": ([vp, ctypes.POINTER(i64), i32], i32),
             "nls_server_destroy": ([vp], i32),
-            "nls_probe_rcp": ([vp, vp, i64, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -253,11 +252,6 @@ def nls_server_wait(s, ticket: int, timeout_ms: int = -1):
         return None
     _gcheck(rc)
     return sv.value, ts.value, td.value
-
-
-def nls_probe_rcp(x, y, n, stream=0) -> None:
-    """Device reciprocal of the FP64 LU pivots on raw DEVICE addresses."""
-    _gcheck(load_library().nls_probe_rcp(x or None, y or None, n, ctypes.c_void_p(stream or None)))
 
 
 def nls_server_now(s) -> float:

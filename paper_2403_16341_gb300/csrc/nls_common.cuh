@@ -79,22 +79,7 @@ NLS_DI uint64_t max_mag_bits(const double (&v)[N])
 
 NLS_DI double bits_to_double(uint64_t b) { return __longlong_as_double((long long)b); }
 
-// 1/x in FP64 for the LU pivots: the FP32 hardware reciprocal refined by two
-// Newton-Raphson steps r <- r + r (1 - x r) (relative error 2^-23 -> 2^-46 ->
-// below 2^-52, within one ulp of the correctly rounded value).  It costs two
-// conversions and four DFMA on GB300's scarce FP64 pipe instead of the longer
-// correctly rounded sequence.  Arguments whose exponent lies outside the FP32
-// normal range (and zero, Inf, NaN) take __drcp_rn.
-NLS_DI double rcp(double x)
-{
-    const uint32_t e = ((uint32_t)((unsigned long long)__double_as_longlong(x) >> 52)) & 0x7FFu;
-    if (e < 1023u - 120u || e > 1023u + 120u) return __drcp_rn(x);
-    double r = double(__frcp_rn(float(x)));
-    double t = fma(-x, r, 1.0);
-    r = fma(r, t, r);
-    t = fma(-x, r, 1.0);
-    return fma(r, t, r);
-}
+NLS_DI double rcp(double x) { return __drcp_rn(x); }
 NLS_DI float rcp(float x) { return __frcp_rn(x); }
 NLS_DI double nls_sqrt(double x) { return __dsqrt_rn(x); }
 NLS_DI float nls_sqrt(float x) { return __fsqrt_rn(x); }
