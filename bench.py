@@ -374,8 +374,12 @@ def run_ours(args, world, rank, local):
     if not args.no_autotune:
         for i, (name, alg) in enumerate(VARIANTS):
             us[i].copy_(u0)
-            t = solver.autotune(batch.family, params, us[i], alg, ABSTOL, MAXITERS)
-            chosen[name] = {1 << 10: "thread", 1 << 11: "warp", 1 << 12: "cta"}[t]
+            solver.autotune(batch.family, params, us[i], alg, ABSTOL, MAXITERS)
+            e = nls.nls_tune_lookup(solver.h, batch.family, N_SYS, alg)
+            mode = ("one block per 32 instances" if e["refill"] == -2 else
+                    f"persistent, refill at {e['refill'] if e['refill'] >= 0 else 24} lanes")
+            chosen[name] = {1 << 10: "thread", 1 << 11: "warp", 1 << 12: "cta"}[e["tiles"]] + \
+                (f" ({e['lanes']} lanes)" if e["lanes"] else "") + ", " + mode
     for _ in range(max(args.warmup, 3)):
         finish(step())
     torch.cuda.synchronize()

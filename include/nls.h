@@ -176,7 +176,7 @@ int nls_set_option(nls_handle h, int option, int64_t value);
 /* Autotuner: times each tiling that can hold n -- thread (n <= 8), warp with
  * 8, 16 or 32 lanes (n <= lanes), CTA (n > 8) -- each both as a persistent
  * grid (thread tiling: refill thresholds 0/16/24/31) and as a
- * one-block-per-chunk grid, on the first min(batch, 65536) instances of this
+ * one-block-per-chunk grid (best of three runs), on the first min(batch, 2^18) instances of this
  * batch; keeps the fastest for (family, n, algorithm, precision) in the
  * handle's table and restores u.  Later nls_solve calls without a tiling
  * flag use the table (a request flushed alone takes the tuned launch mode;
@@ -187,6 +187,12 @@ int nls_set_option(nls_handle h, int option, int64_t value);
  * the table is read from it. */
 int nls_autotune(nls_handle h, int family, const double *params, double *u, int n, int64_t batch,
                  int alg, double abstol, int maxiters, int *chosen);
+/* The tuned entry for (family, n, alg): tiling flag, warp lanes, refill
+ * (-2 one-block-per-chunk grid, -1 persistent with the handle's threshold,
+ * >= 0 persistent with that threshold) and the measured instances/s.
+ * NLS_E_NOTFOUND when (family, n, alg) has not been tuned. */
+int nls_tune_lookup(nls_handle h, int family, int n, int alg, int *tiles, int *lanes, int *refill,
+                    double *rate);
 /* Write / read the tuning table (text: family n alg tiles lanes refill rate;
  * refill -2 = one-block-per-chunk grid, -1 = persistent with the handle's
  * threshold, >= 0 = persistent with that threshold). */

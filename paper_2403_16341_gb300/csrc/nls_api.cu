@@ -500,7 +500,7 @@ static int tune_trial(nls_batch *h, const SolveArgs &base, const KernelInfo &k, 
     NLS_CUDA(h, cudaEventCreate(&e0));
     NLS_CUDA(h, cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int rep = 0; rep < 2; ++rep) {
+    for (int rep = 0; rep < 3; ++rep) {
         NLS_CUDA(h, cudaMemcpy2DAsync(base.u, base.ld * 8, save, S * 8, S * 8, base.n, cudaMemcpyDeviceToDevice,
                                       h->stream));
         NLS_CUDA(h, cudaMemsetAsync(ctr, 0, 16, h->stream));
@@ -694,7 +694,7 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
     rc = flush_pending(h);
     if (rc) return rc;
     if (batch == 0) return NLS_OK;
-    const int64_t S = std::min<int64_t>(batch, 1 << 16);
+    const int64_t S = std::min<int64_t>(batch, 1 << 18);
     const size_t need = (size_t)n * (size_t)S * 8 + 256;
     if (need > h->tune_bytes) {
         NLS_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -753,6 +753,19 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
     NLS_CUDA(h, cudaStreamSynchronize(h->stream));
     h->tuned[tune_key(family, n, alg)] = best;
     if (chosen) *chosen = best.tiles;
+    return NLS_OK;
+}
+
+int nls_tune_lookup(nls_handle h, int family, int n, int alg, int *tiles, int *lanes, int *refill,
+                    double *rate)
+{
+    if (!h) return NLS_E_INVALID;
+    auto it = h->tuned.find(tune_key(family, n, alg));
+    if (it == h->tuned.end()) return fail(h, NLS_E_NOTFOUND, "no tuned entry for family %d, n = %d", family, n);
+    if (tiles) *tiles = it->second.tiles;
+    if (lanes) *lanes = it->second.lanes;
+    if (refill) *refill = it->second.refill;
+    if (rate) *rate = it->second.rate;
     return NLS_OK;
 }
 
