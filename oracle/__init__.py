@@ -9,5 +9,5 @@ from .oracle import (  # noqa: F401
     ALG_NEWTON, ALG_NEWTON_BACKTRACK, ALG_TRUST_DOGLEG,
     ST_SUCCESS, ST_MAXITERS, ST_SINGULAR, ST_NONFINITE, ST_LS_FAILED, ST_TR_STALLED,
     build, residual, jacobian, lu_factor, lu_solve, dogleg, solve_one, solve_trace,
-    solve_batch, polish, polish_batch,
+    solve_batch, polish, polish_batch, adjoint,
 )

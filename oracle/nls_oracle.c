@@ -494,3 +494,52 @@ double oracle_polish(int family, int n, const double *p, double *u, int maxsteps
     free(LU);
     return fn;
 }
+
+/* ---------------------------------------------------------------- sensitivity */
+
+/* Adjoint sensitivity at a root u (Sec. 2.3, implicit function theorem):
+ * with J = dF/du at u, du/dtheta = -J^{-1} dF/dtheta (the sign the printed
+ * formula drops), so for a cotangent w = dL/du,
+ *     dL/dtheta = -mu^T dF/dtheta,   J^T mu = w.
+ * grad receives dL/dtheta in the family's parameter order (E values).
+ * Returns 0, or 1 if J is singular. */
+int oracle_adjoint(int family, int n, const double *p, const double *u, const double *w,
+                   double *grad)
+{
+    size_t nn = (size_t)n * (size_t)n;
+    double *J = malloc(sizeof(double) * (2 * nn + (size_t)n));
+    double *Jt = J + nn, *mu = Jt + nn;
+    int *piv = malloc(sizeof(int) * (size_t)n);
+    int i, j, rc = 0;
+    oracle_jacobian(family, n, p, u, J);
+    for (i = 0; i < n; i++)
+        for (j = 0; j < n; j++)
+            Jt[i * n + j] = J[j * n + i];
+    if (oracle_lu_factor(n, Jt, piv) != 0) {
+        rc = 1;
+        goto done;
+    }
+    oracle_lu_solve(n, Jt, piv, w, mu);
+    if (family == FAM_CUBIC) {
+        /* dF_i/dA_ij = u_j, dF_i/db_i = -1 */
+        for (i = 0; i < n; i++) {
+            for (j = 0; j < n; j++)
+                grad[i * n + j] = -mu[i] * u[j];
+            grad[n * n + i] = mu[i];
+        }
+    } else if (family == FAM_BRATU) {
+        /* dF_i/dlambda = exp(u_i) */
+        double s = 0.0;
+        for (i = 0; i < n; i++)
+            s += mu[i] * exp(u[i]);
+        grad[0] = -s;
+    } else if (family == FAM_SQUARE) {
+        /* dF_i/dp_i = -1 */
+        for (i = 0; i < n; i++)
+            grad[i] = mu[i];
+    }
+done:
+    free(piv);
+    free(J);
+    return rc;
+}

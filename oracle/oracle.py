@@ -63,6 +63,8 @@ def _load():
                                                ctypes.c_double, ctypes.c_int, _I, _I, _D, _I]
             lib.oracle_polish.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_int]
             lib.oracle_polish.restype = ctypes.c_double
+            lib.oracle_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
+            lib.oracle_adjoint.restype = ctypes.c_int
             lib.oracle_n_params.argtypes = [ctypes.c_int, ctypes.c_int]
             lib.oracle_n_params.restype = ctypes.c_int
             _lib = lib
@@ -196,3 +198,14 @@ def polish_batch(family: int, params, u, maxsteps: int = 8) -> np.ndarray:
         p = params[:, k] if params.shape[0] else np.zeros(1)
         u[:, k], _ = polish(family, p, u[:, k], maxsteps)
     return u
+
+
+def adjoint(family: int, p, u, w):
+    """dL/dtheta at the root u for the cotangent w = dL/du (implicit function
+    theorem).  Returns (grad[E], singular)."""
+    p = _f64(p) if np.size(p) else np.zeros(1)
+    u, w = _f64(u), _f64(w)
+    E = _load().oracle_n_params(family, u.size)
+    g = np.zeros(max(E, 1))
+    rc = _load().oracle_adjoint(family, u.size, _dp(p), _dp(u), _dp(w), _dp(g))
+    return g[:E], bool(rc)

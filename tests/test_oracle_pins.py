@@ -431,3 +431,46 @@ def test_threaded_batch_equals_serial():
     r4 = O.solve_batch(b.family, b.params, b.u0, O.ALG_TRUST_DOGLEG, threads=4)
     for a, c in zip(r1, r4):
         np.testing.assert_array_equal(a, c)
+
+
+# ---------------------------------------------------------------- sensitivity (Sec. 2.3)
+
+def test_adjoint_square_example_sec2_3():
+    # g(u*) = sum u*^2 with u* = sqrt(p): dg/dp = 1 exactly (the example's gradient)
+    g = golden("square_sec2_3.json")
+    u, st, *_ = O.solve_one(SQUARE, g["p"], g["u0"], O.ALG_NEWTON, abstol=1e-14)
+    grad, sing = O.adjoint(SQUARE, g["p"], u, 2.0 * u)
+    assert not sing
+    np.testing.assert_allclose(grad, g["dg_dtheta"], rtol=1e-15)
+    # du*/dp = 1 / (2 sqrt(p)): cotangent e_i picks row i
+    for i in range(2):
+        e = np.zeros(2)
+        e[i] = 1.0
+        grad, _ = O.adjoint(SQUARE, g["p"], u, e)
+        np.testing.assert_allclose(grad[i], 0.5 / np.sqrt(g["p"][i]), rtol=1e-15)
+        assert grad[1 - i] == 0.0
+
+
+@pytest.mark.parametrize("family,n", [(CUBIC, 3), (CUBIC, 6), (BRATU, 5), (SQUARE, 4)])
+def test_adjoint_matches_finite_differences(family, n):
+    rng = np.random.default_rng(7)
+    if family == CUBIC:
+        b = I.cubic_batch(n, 1, config_id=8)
+    elif family == BRATU:
+        b = I.bratu_batch(n, 1, config_id=8)
+    else:
+        b = I.square_batch(n, 1)
+    p = b.params[:, 0].copy()
+    u, st, *_ = O.solve_one(family, p, b.u0[:, 0], O.ALG_NEWTON, abstol=1e-14)
+    w = rng.normal(size=n)
+    grad, sing = O.adjoint(family, p, u, w)
+    assert not sing
+    for e in range(p.size):
+        h = 1e-6 * max(1.0, abs(p[e]))
+        pp, pm = p.copy(), p.copy()
+        pp[e] += h
+        pm[e] -= h
+        up, *_ = O.solve_one(family, pp, u, O.ALG_NEWTON, abstol=1e-15)
+        um, *_ = O.solve_one(family, pm, u, O.ALG_NEWTON, abstol=1e-15)
+        fd = w @ (up - um) / (2 * h)
+        assert abs(grad[e] - fd) <= 1e-6 * (1 + abs(fd)), (e, grad[e], fd)
