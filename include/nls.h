@@ -127,6 +127,19 @@ int nls_batch_create(nls_handle *out, int device, void *cuda_stream, size_t mem_
 int nls_solve(nls_handle h, int family, const double *params, double *u, int n, int64_t batch,
               int alg, double abstol, int maxiters, const nls_outputs *out, int64_t *req);
 
+/* Sensitivity of the roots to the parameters (Sec. 2.3, implicit function
+ * theorem).  At roots u (DEVICE float64[n * batch], e.g. from nls_solve) with
+ * J = dF/du, du/dtheta = -J^{-1} dF/dtheta; for cotangents w = dL/du (DEVICE
+ * float64[n * batch]) this computes, per instance, mu from J^T mu = w and
+ * grad = dL/dtheta = -mu^T dF/dtheta (DEVICE float64[E * batch], the family's
+ * parameter layout).  status (DEVICE int32[batch], may be NULL) receives
+ * NLS_SUCCESS or NLS_SINGULAR.  FP64, one instance per thread, n <= 8.
+ * Enqueued on the handle's stream at once (not grouped with nls_solve
+ * requests); order it after the solve that produced u.
+ * Errors: NLS_E_INVALID, NLS_E_UNSUPPORTED (n > 8, unknown family), NLS_E_CUDA. */
+int nls_adjoint(nls_handle h, int family, const double *params, const double *u, int n,
+                int64_t batch, const double *w, double *grad, int32_t *status);
+
 /* Launch every pending request of the handle on its stream (asynchronous). */
 int nls_flush(nls_handle h);
 

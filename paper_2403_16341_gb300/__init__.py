@@ -43,7 +43,7 @@ EXPORTED = ("nls_batch_create", "nls_solve", "nls_flush", "nls_status", "nls_sol
             "nls_batch_destroy", "nls_last_error", "nls_launch_count", "nls_set_option",
             "nls_solve_noalloc", "nls_autotune", "nls_tune_save", "nls_tune_load",
             "nls_server_create", "nls_server_submit", "nls_server_wait", "nls_server_now",
-            "nls_server_stats", "nls_server_destroy", "nls_tune_lookup")
+            "nls_server_stats", "nls_server_destroy", "nls_tune_lookup", "nls_adjoint")
 NLS_NOALLOC_MAX_GROUPS = 64
 
 
@@ -97,6 +97,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "nls_autotune": ([vp, i32, vp, vp, i32, i64, i32, dbl, i32,
                               ctypes.POINTER(ctypes.c_int)], i32),
             "nls_tune_save": ([vp, ctypes.c_char_p], i32),
+            "nls_adjoint": ([vp, i32, vp, vp, i32, i64, vp, vp, vp], i32),
             "nls_tune_lookup": ([vp, i32, i32, i32, ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(dbl)], i32),
@@ -215,6 +216,12 @@ def nls_autotune(h, family, params, u, n, batch, alg, abstol, maxiters) -> int:
     _check(h, load_library().nls_autotune(h, family, params or None, u or None, n, batch, alg,
                                           abstol, maxiters, ctypes.byref(chosen)))
     return chosen.value
+
+
+def nls_adjoint(h, family, params, u, n, batch, w, grad, status=0) -> None:
+    """dL/dtheta at the roots for cotangents w (raw DEVICE addresses)."""
+    _check(h, load_library().nls_adjoint(h, family, params or None, u or None, n, batch,
+                                         w or None, grad or None, status or None))
 
 
 def nls_tune_lookup(h, family, n, alg) -> dict:

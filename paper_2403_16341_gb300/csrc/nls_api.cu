@@ -756,6 +756,24 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
     return NLS_OK;
 }
 
+int nls_adjoint(nls_handle h, int family, const double *params, const double *u, int n, int64_t batch,
+                const double *w, double *grad, int32_t *status)
+{
+    if (!h) return NLS_E_INVALID;
+    if (family < 0 || family > FAM_ROSENBROCK) return fail(h, NLS_E_UNSUPPORTED, "unknown family %d", family);
+    if (n < 1 || n > 8) return fail(h, NLS_E_UNSUPPORTED, "nls_adjoint holds n <= 8 (n = %d)", n);
+    if (batch < 0) return fail(h, NLS_E_INVALID, "negative batch");
+    if (batch == 0) return NLS_OK;
+    if (!u || !w) return fail(h, NLS_E_INVALID, "u or w is NULL");
+    if (n_params(family, n) > 0 && (!params || !grad)) return fail(h, NLS_E_INVALID, "params or grad is NULL");
+    if ((batch + 31) / 32 > INT32_MAX) return fail(h, NLS_E_INVALID, "batch too large");
+    NLS_CUDA(h, cudaSetDevice(h->device));
+    cudaError_t e = nls::launch_adjoint(family, n, params, u, w, grad, status, batch, h->stream);
+    if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "adjoint launch: %s", cudaGetErrorString(e));
+    ++h->launches;
+    return NLS_OK;
+}
+
 int nls_tune_lookup(nls_handle h, int family, int n, int alg, int *tiles, int *lanes, int *refill,
                     double *rate)
 {
