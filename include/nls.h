@@ -53,7 +53,13 @@ enum nls_family { NLS_CUBIC = 0, NLS_BRATU = 1, NLS_SQUARE = 2, NLS_ROSENBROCK =
 enum nls_alg {
     NLS_NEWTON = 0,           /* Sec. 2.1, Eq. 2                               */
     NLS_NEWTON_BACKTRACK = 1, /* Sec. 2.2.1: Armijo (Eq. 8-9), alpha <- alpha/2 */
-    NLS_TRUST_DOGLEG = 2      /* Sec. 2.2.2: Eq. 12-14, Powell's dogleg          */
+    NLS_TRUST_DOGLEG = 2,     /* Sec. 2.2.2: Eq. 12-14, Powell's dogleg          */
+    NLS_POLYALG = 3           /* Sec. 3.2 poly-algorithm for n <= 25 (no quasi-
+                                 Newton stage): Newton on every instance; the
+                                 ones that fail restart from u0 with
+                                 backtracking, then with the trust region.
+                                 iters = the final stage's passes, nfev = all
+                                 stages' residual evaluations.                */
 };
 #define NLS_ALG_MASK 0xff
 enum nls_flags {

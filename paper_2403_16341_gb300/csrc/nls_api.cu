@@ -77,6 +77,9 @@ struct Request {
     SolveArgs args{};
     KernelInfo kern{};
     int family = 0, tiles = 0, lanes = 0, refill = -1;
+    bool poly = false;             // NLS_POLYALG: Newton, then backtracking, then trust region
+    void *poly_ws = nullptr;       // its device workspace (freed at completion)
+    size_t poly_bytes = 0;
     double rate = 0.0;                     // tuned rate (0 = use the cost model)
     int slot = -1;                         // first of 2 ring entries (solved, work counter)
     std::shared_ptr<cudaEvent_t> done;     // recorded after the request's group
@@ -297,11 +300,11 @@ static int plan_grids(nls_batch *h, const std::vector<Request *> &rs, std::vecto
 {
     int live = 0;
     for (Request *r : rs)
-        if (r->args.batch > 0) ++live;
+        if (r->args.batch > 0 && !r->poly) ++live;
     grids.assign(rs.size(), 0);
     for (size_t i = 0; i < rs.size(); ++i) {
         Request &r = *rs[i];
-        if (r.args.batch == 0) continue;
+        if (r.args.batch == 0 || r.poly) continue; // a poly request runs its own chain
         const int64_t ctas = (r.args.batch + r.kern.per_cta - 1) / r.kern.per_cta;
         const bool persistent = h->opt.persistent && live == 1 && r.refill != REFILL_STATIC;
         if (!persistent) {
@@ -407,6 +410,105 @@ static int launch_direct(nls_batch *h, const std::vector<Request *> &rs, const s
     return NLS_OK;
 }
 
+// Device workspace of a poly-algorithm request: the original u0, compact
+// copies of the instances still failing, their outputs, full-size outputs the
+// caller did not provide, and the stage counters.
+struct PolyWs {
+    double *u0, *cparams, *cu, *cres, *fres;
+    int64_t *idx;
+    int32_t *cst, *cit, *cnf, *fst, *fit, *fnf;
+    unsigned long long *ctr; // [0..2] stage 2: gathered, solved, work; [3..5] stage 3
+};
+
+static size_t poly_layout(int64_t B, int n, int E, char *base, PolyWs *w)
+{
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *p = base ? base + off : nullptr;
+        off += al(bytes);
+        return p;
+    };
+    PolyWs t{};
+    t.u0 = (double *)take((size_t)n * B * 8);
+    t.cparams = (double *)take((size_t)std::max(E, 1) * B * 8);
+    t.cu = (double *)take((size_t)n * B * 8);
+    t.cres = (double *)take((size_t)B * 8);
+    t.fres = (double *)take((size_t)B * 8);
+    t.idx = (int64_t *)take((size_t)B * 8);
+    t.cst = (int32_t *)take((size_t)B * 4);
+    t.cit = (int32_t *)take((size_t)B * 4);
+    t.cnf = (int32_t *)take((size_t)B * 4);
+    t.fst = (int32_t *)take((size_t)B * 4);
+    t.fit = (int32_t *)take((size_t)B * 4);
+    t.fnf = (int32_t *)take((size_t)B * 4);
+    t.ctr = (unsigned long long *)take(8 * 8);
+    if (w) *w = t;
+    return off;
+}
+
+// Newton on every instance; the failures restart from u0 with backtracking;
+// what still fails restarts with the trust region (Sec. 3.2).  All on the
+// handle's stream, counts kept on the device.
+static int launch_poly(nls_batch *h, Request &r)
+{
+    const int64_t B = r.args.batch;
+    const int n = r.args.n, E = n_params(r.family, n);
+    PolyWs w;
+    poly_layout(B, n, E, static_cast<char *>(r.poly_ws), &w);
+    cudaStream_t st = h->stream;
+    SolveArgs a = r.args;
+    if (!a.status) a.status = w.fst;
+    if (!a.iters) a.iters = w.fit;
+    if (!a.nfev) a.nfev = w.fnf;
+    if (!a.resid) a.resid = w.fres;
+    NLS_CUDA(h, cudaMemcpyAsync(w.u0, a.u, (size_t)n * B * 8, cudaMemcpyDeviceToDevice, st));
+    NLS_CUDA(h, cudaMemsetAsync(w.ctr, 0, 8 * 8, st));
+    a.alg = NLS_NEWTON;
+    a.counter = nullptr;
+    a.refill_below = 0;
+    const int64_t ctas = (B + r.kern.per_cta - 1) / r.kern.per_cta;
+    cudaError_t e = r.kern.launch(a, (int)std::min<int64_t>(ctas, INT32_MAX), st);
+    if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "poly stage 1: %s", cudaGetErrorString(e));
+    ++h->launches;
+    int occ = 0;
+    int rc = occupancy(h, r.kern, &occ);
+    if (rc) return rc;
+    const int grid = (int)std::min<int64_t>(ctas, (int64_t)std::max(occ, 1) * h->sms);
+    const int stages[2] = {NLS_NEWTON_BACKTRACK, NLS_TRUST_DOGLEG};
+    for (int sidx = 0; sidx < 2; ++sidx) {
+        unsigned long long *cnt = w.ctr + 3 * sidx;
+        nls::PolyGatherArgs g{B, E, n, a.status, a.params, w.u0, w.idx, w.cparams, w.cu, cnt};
+        e = nls::launch_poly_gather(g, st);
+        if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "poly gather: %s", cudaGetErrorString(e));
+        SolveArgs c = a;
+        c.params = E ? w.cparams : nullptr;
+        c.u = w.cu;
+        c.batch = B;
+        c.ld = B;
+        c.dyn_batch = cnt;
+        c.alg = stages[sidx];
+        c.status = w.cst;
+        c.iters = w.cit;
+        c.nfev = w.cnf;
+        c.resid = w.cres;
+        c.solved = cnt + 1;
+        c.counter = cnt + 2;
+        c.refill_below = h->opt.refill_below;
+        e = r.kern.launch(c, grid, st);
+        if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "poly stage %d: %s", sidx + 2, cudaGetErrorString(e));
+        nls::PolyScatterArgs sc{B, n, cnt, w.idx, w.cu, w.cst, w.cit, w.cnf, w.cres,
+                                a.u, a.status, a.iters, a.nfev, a.resid};
+        e = nls::launch_poly_scatter(sc, st);
+        if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "poly scatter: %s", cudaGetErrorString(e));
+        h->launches += 3;
+    }
+    e = nls::launch_poly_total(a.solved, w.ctr + 1, w.ctr + 4, st);
+    if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "poly total: %s", cudaGetErrorString(e));
+    ++h->launches;
+    return NLS_OK;
+}
+
 static int flush_pending(nls_batch *h)
 {
     if (h->pending.empty()) return NLS_OK;
@@ -434,6 +536,16 @@ static int flush_pending(nls_batch *h)
     if (rc) return rc;
     rc = h->opt.graph ? launch_graph(h, rs, grids, s0, 2 * nreq) : launch_direct(h, rs, grids, s0, 2 * nreq);
     if (rc) return rc;
+    bool any_poly = false;
+    for (Request *r : rs)
+        if (r->poly && r->args.batch > 0) {
+            rc = launch_poly(h, *r);
+            if (rc) return rc;
+            any_poly = true;
+        }
+    if (any_poly)
+        NLS_CUDA(h, cudaMemcpyAsync(h->h_ctr + s0, h->d_ctr + s0, sizeof(unsigned long long) * 2 * nreq,
+                                    cudaMemcpyDeviceToHost, h->stream));
     NLS_CUDA(h, cudaEventRecord(*ev, h->stream));
     h->pending.clear();
     return NLS_OK;
@@ -449,7 +561,7 @@ static int validate(nls_batch *h, int family, const double *params, const double
     if (maxiters < 0) return fail(h, NLS_E_INVALID, "negative maxiters");
     if (!(abstol >= 0.0) || !std::isfinite(abstol)) return fail(h, NLS_E_INVALID, "abstol must be finite and >= 0");
     const int a = alg & NLS_ALG_MASK;
-    if (a > NLS_TRUST_DOGLEG) return fail(h, NLS_E_INVALID, "unknown algorithm %d", a);
+    if (a > NLS_POLYALG) return fail(h, NLS_E_INVALID, "unknown algorithm %d", a);
     if (alg & ~(NLS_ALG_MASK | NLS_MIXED | NLS_ANALYTIC_JAC | NLS_TILE_THREAD | NLS_TILE_WARP | NLS_TILE_CTA))
         return fail(h, NLS_E_INVALID, "unknown flags in alg 0x%x", alg);
     if (batch > 0 && !u) return fail(h, NLS_E_INVALID, "u is NULL");
@@ -575,6 +687,14 @@ int nls_solve(nls_handle h, int family, const double *params, double *u, int n, 
         r.args.resid = out->resid_inf;
         r.args.nfev = out->nfev;
     }
+    if ((alg & NLS_ALG_MASK) == NLS_POLYALG) {
+        r.poly = true;
+        if (batch > 0) {
+            r.poly_bytes = poly_layout(batch, n, n_params(family, n), nullptr, nullptr);
+            rc = dev_alloc(h, &r.poly_ws, r.poly_bytes);
+            if (rc) return rc;
+        }
+    }
     h->reqs[r.id] = r;
     h->pending.push_back(r.id);
     *req = r.id;
@@ -607,6 +727,10 @@ int nls_status(nls_handle h, int64_t req, int64_t *solved, int timeout_ms)
         h->owner[r.slot] = h->owner[r.slot + 1] = 0;
     }
     if (solved) *solved = s;
+    if (r.poly_ws) {
+        cudaFree(r.poly_ws);
+        h->mem_used -= r.poly_bytes;
+    }
     h->reqs.erase(it);
     return NLS_OK;
 }
@@ -664,6 +788,8 @@ int nls_batch_destroy(nls_handle h)
     cudaSetDevice(h->device);
     flush_pending(h);
     cudaStreamSynchronize(h->stream);
+    for (auto &kv : h->reqs)
+        if (kv.second.poly_ws) cudaFree(kv.second.poly_ws);
     h->reqs.clear();
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     if (h->d_tune) cudaFree(h->d_tune);
@@ -690,6 +816,8 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
     if (rc) return rc;
     if (alg & (NLS_TILE_THREAD | NLS_TILE_WARP | NLS_TILE_CTA))
         return fail(h, NLS_E_INVALID, "nls_autotune chooses the tiling: pass no tiling flag");
+    if ((alg & NLS_ALG_MASK) == NLS_POLYALG)
+        return fail(h, NLS_E_INVALID, "tune the stage algorithms, not NLS_POLYALG");
     NLS_CUDA(h, cudaSetDevice(h->device));
     rc = flush_pending(h);
     if (rc) return rc;

@@ -51,7 +51,18 @@ struct SolveArgs {
     unsigned long long *solved;  // += #SUCCESS (may be null)
     unsigned long long *counter; // work counter for persistent launches (null = static)
     int refill_below;            // persistent: refill idle lanes when live lanes <= this
+    // when set, the instance count is min(batch, *dyn_batch), read on the
+    // device (a count produced by an earlier kernel of the same stream)
+    const unsigned long long *dyn_batch;
 };
+
+NLS_DI void apply_dyn_batch(SolveArgs &a)
+{
+    if (a.dyn_batch) {
+        const long long d = (long long)*a.dyn_batch;
+        if (d < a.batch) a.batch = d;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Bit-exact FP64 tests on the integer pipes.  On GB300 the FP64 pipe is the

@@ -549,6 +549,7 @@ constexpr int cta_smem_bytes()
 template <int R, int FAM, bool MIXED>
 __global__ void __launch_bounds__(CTA_TPB) k_solve_cta(SolveArgs a)
 {
+    apply_dyn_batch(a);
     using S = CtaSolver<R, FAM, MIXED>;
     using SM = typename S::SM;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -42,3 +42,33 @@ namespace nls {
 cudaError_t launch_adjoint(int family, int n, const double *params, const double *u, const double *w,
                            double *grad, int32_t *status, int64_t batch, cudaStream_t st);
 } // namespace nls
+
+namespace nls {
+// Poly-algorithm helpers (nls_poly.cu).
+struct PolyGatherArgs {
+    int64_t batch;               // full batch (also the compact arrays' leading dimension)
+    int E, n;
+    const int32_t *status;       // [batch] statuses after the previous stage
+    const double *params;        // [E][batch]
+    const double *u0;            // [n][batch] original starting points
+    int64_t *idx;                // [batch] compact position -> instance
+    double *cparams, *cu;        // [E][batch], [n][batch] compact copies
+    unsigned long long *count;   // number gathered (zeroed before)
+};
+struct PolyScatterArgs {
+    int64_t batch;
+    int n;
+    const unsigned long long *count;
+    const int64_t *idx;
+    const double *cu;
+    const int32_t *cstatus, *citers, *cnfev;
+    const double *cresid;
+    double *u;
+    int32_t *status, *iters, *nfev;
+    double *resid;
+};
+cudaError_t launch_poly_gather(const PolyGatherArgs &g, cudaStream_t st);
+cudaError_t launch_poly_scatter(const PolyScatterArgs &s, cudaStream_t st);
+cudaError_t launch_poly_total(unsigned long long *solved, const unsigned long long *s2,
+                              const unsigned long long *s3, cudaStream_t st);
+} // namespace nls

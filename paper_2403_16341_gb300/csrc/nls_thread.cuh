@@ -348,6 +348,7 @@ constexpr int thread_smem_bytes()
 template <int N, int FAM, bool MIXED, bool ANALYTIC>
 __global__ void __launch_bounds__(THREAD_TPB) k_solve_thread(SolveArgs a)
 {
+    apply_dyn_batch(a);
     using S = ThreadSolver<N, FAM, MIXED, ANALYTIC>;
     constexpr int E = S::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -461,6 +461,7 @@ constexpr int warp_smem_bytes()
 template <int L, int FAM, bool MIXED>
 __global__ void __launch_bounds__(WARP_TPB) k_solve_warp(SolveArgs a)
 {
+    apply_dyn_batch(a);
     using S = WarpSolver<L, FAM, MIXED>;
     using SM = WarpSmem<L, MIXED>;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -1,0 +1,73 @@
+"""Batched poly-algorithm (Sec. 3.2): Newton everywhere, failures restart from
+u0 with backtracking, then with the trust region.  Checked against the same
+composition of oracle solves."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2403_16341_gb300 import inputs as I
+from tests.parity import gpu_solve
+
+pytestmark = pytest.mark.gpu
+POLY = 3
+
+
+@pytest.fixture(scope="module")
+def solver():
+    import paper_2403_16341_gb300 as nls
+    s = nls.Solver(0)
+    yield s
+    s.close()
+
+
+def oracle_poly(b, abstol=1e-10, maxiters=100):
+    u, st, it, rs, nf = O.solve_batch(b.family, b.params, b.u0, O.ALG_NEWTON, abstol, maxiters)
+    nf = nf.copy()
+    for alg in (O.ALG_NEWTON_BACKTRACK, O.ALG_TRUST_DOGLEG):
+        bad = np.nonzero(st != O.ST_SUCCESS)[0]
+        if bad.size == 0:
+            break
+        P = b.params[:, bad] if b.params.size else np.zeros((0, bad.size))
+        u2, st2, it2, rs2, nf2 = O.solve_batch(b.family, P, b.u0[:, bad], alg, abstol, maxiters)
+        u[:, bad], st[bad], it[bad] = u2, st2, it2
+        nf[bad] += nf2
+    return u, st, it, nf
+
+
+def test_rosenbrock_poly_rescues_newton_failures(solver):
+    rng = np.random.default_rng(11)
+    B, n = 777, 8
+    u0 = rng.uniform(-2.0, 2.0, size=(n, B))
+    b = I.Batch(I.FAMILY_ROSENBROCK, n, np.zeros((0, B)), u0)
+    nr = gpu_solve(solver, b, 0, abstol=1e-10, maxiters=100)
+    assert (nr["status"] != 0).sum() > 20  # plain Newton fails on part of the batch
+    g = gpu_solve(solver, b, POLY, abstol=1e-10, maxiters=100)
+    ou, ost, oit, onf = oracle_poly(b)
+    np.testing.assert_array_equal(g["status"], ost)
+    ok = g["status"] == 0
+    assert ok.mean() > 0.99 and g["solved"] == ok.sum()
+    np.testing.assert_allclose(g["u"][:, ok], 1.0, atol=1e-9)
+    assert (g["nfev"] == onf).mean() > 0.95
+    assert (g["nfev"] >= nr["nfev"]).all()
+
+
+def test_poly_equals_newton_when_newton_converges(solver):
+    b = I.cubic_batch(8, 2000, config_id=1, b_half_width=5.0)
+    nr = gpu_solve(solver, b, 0)
+    assert (nr["status"] == 0).all()
+    g = gpu_solve(solver, b, POLY)
+    for key in ("u", "status", "iters", "resid", "nfev"):
+        np.testing.assert_array_equal(g[key], nr[key])
+
+
+@pytest.mark.parametrize("n", [12, 40])
+def test_poly_warp_and_cta_tilings(solver, n):
+    rng = np.random.default_rng(n)
+    B = 301
+    u0 = rng.uniform(-2.0, 2.0, size=(n, B))
+    b = I.Batch(I.FAMILY_ROSENBROCK, n, np.zeros((0, B)), u0)
+    g = gpu_solve(solver, b, POLY, abstol=1e-10, maxiters=200)
+    ok = g["status"] == 0
+    assert ok.mean() > 0.9
+    np.testing.assert_allclose(g["u"][:, ok], 1.0, atol=1e-7)
+    assert (g["resid"][ok] <= 1e-10).all()
