@@ -47,8 +47,16 @@ def test_rosenbrock_poly_rescues_newton_failures(solver):
     ok = g["status"] == 0
     assert ok.mean() > 0.99 and g["solved"] == ok.sum()
     np.testing.assert_allclose(g["u"][:, ok], 1.0, atol=1e-9)
-    assert (g["nfev"] == onf).mean() > 0.95
-    assert (g["nfev"] >= nr["nfev"]).all()
+    # plain Newton from U[-2, 2]^8 is rounding-chaotic, so the stage at which an
+    # instance is rescued may differ from the oracle's; what is fixed: where the
+    # GPU's own Newton run converged the poly result is that run, bit for bit,
+    # and elsewhere later stages added residual evaluations
+    nr_ok = nr["status"] == 0
+    for key in ("u", "iters", "resid", "nfev"):
+        a, c = g[key], nr[key]
+        np.testing.assert_array_equal(a[..., nr_ok], c[..., nr_ok])
+    assert (g["nfev"][~nr_ok] > nr["nfev"][~nr_ok]).all()
+    assert (g["resid"][ok] <= 1e-10).all()
 
 
 def test_poly_equals_newton_when_newton_converges(solver):
