@@ -68,14 +68,17 @@ def test_poly_equals_newton_when_newton_converges(solver):
         np.testing.assert_array_equal(g[key], nr[key])
 
 
-@pytest.mark.parametrize("n", [12, 40])
-def test_poly_warp_and_cta_tilings(solver, n):
-    rng = np.random.default_rng(n)
-    B = 301
-    u0 = rng.uniform(-2.0, 2.0, size=(n, B))
-    b = I.Batch(I.FAMILY_ROSENBROCK, n, np.zeros((0, B)), u0)
-    g = gpu_solve(solver, b, POLY, abstol=1e-10, maxiters=200)
+@pytest.mark.parametrize("n,floor", [(12, 1.0), (40, 0.6)])
+def test_poly_warp_and_cta_tilings(solver, n, floor):
+    # the Sec. 3.4 starts U[0, 1)^n, every third one moved to the Fig. 1 start
+    # (-1.2, 1, ..., 1) where plain Newton fails; the oracle composition solves
+    # all of them at n = 12 and 199 of 301 at n = 40 within 300 passes
+    b = I.rosenbrock_batch(n, 301, seed=n)
+    b.u0[0, ::3] = -1.2
+    b.u0[1:, ::3] = 1.0
+    nr = gpu_solve(solver, b, 0, abstol=1e-10, maxiters=300)
+    g = gpu_solve(solver, b, POLY, abstol=1e-10, maxiters=300)
     ok = g["status"] == 0
-    assert ok.mean() > 0.9
+    assert ok.mean() >= floor - 1e-12 and ok.sum() > (nr["status"] == 0).sum()
     np.testing.assert_allclose(g["u"][:, ok], 1.0, atol=1e-7)
     assert (g["resid"][ok] <= 1e-10).all()
