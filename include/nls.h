@@ -79,7 +79,8 @@ enum nls_inst_status {
     NLS_NONFINITE = 3,  /* F became Inf/NaN (at u0, or after a full Newton step) */
     NLS_LS_FAILED = 4,  /* 30 backtracking trials without sufficient decrease    */
     NLS_TR_STALLED = 5, /* 32 trust-region rejections in a row                   */
-    NLS_ABORTED = 6     /* not run: the request was cancelled or timed out       */
+    NLS_ABORTED = 6     /* the launch's deadline (NLS_OPT_DEADLINE_US) passed
+                           before convergence; u holds the last iterate        */
 };
 
 enum nls_err {
@@ -184,6 +185,11 @@ enum nls_option {
                                  idle lanes when at most this many lanes are
                                  still iterating (0..31, default 24)           */
     NLS_OPT_CTAS_PER_SM = 3,  /* cap on resident CTAs per SM (0 = occupancy)   */
+    NLS_OPT_DEADLINE_US = 5,  /* > 0: each launch stops iterating this many
+                                 microseconds (device clock) after it starts;
+                                 unfinished instances end NLS_ABORTED.  0 (the
+                                 default): no deadline.  Applies to requests
+                                 enqueued afterwards.                          */
     NLS_OPT_GRAPH = 4         /* 1 (default): a flush is one CUDA-graph launch
                                  (counter reset, one kernel node per request,
                                  all concurrent, counter read-back), cached by

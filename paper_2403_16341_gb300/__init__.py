@@ -38,6 +38,7 @@ NLS_OK, NLS_E_INVALID, NLS_E_CUDA, NLS_E_NOMEM = 0, -1, -2, -3
 NLS_E_UNSUPPORTED, NLS_E_TIMEOUT, NLS_E_BUSY, NLS_E_NOTFOUND = -4, -5, -6, -7
 # nls_option
 NLS_OPT_PERSISTENT, NLS_OPT_REFILL_BELOW, NLS_OPT_CTAS_PER_SM, NLS_OPT_GRAPH = 1, 2, 3, 4
+NLS_OPT_DEADLINE_US = 5
 
 EXPORTED = ("nls_batch_create", "nls_solve", "nls_flush", "nls_status", "nls_solve_host",
             "nls_batch_destroy", "nls_last_error", "nls_launch_count", "nls_set_option",

@@ -92,6 +92,7 @@ struct Opts {
     int refill_below = 24;  // refill idle lanes when running lanes <= this
     int ctas_per_sm = 0;    // 0 = occupancy limit
     int graph = 1;          // flush through a cached CUDA graph
+    int64_t deadline_us = 0; // per-launch iteration budget (0 = none)
 };
 
 // Autotuner result for one (family, n, algorithm, precision).
@@ -681,6 +682,7 @@ int nls_solve(nls_handle h, int family, const double *params, double *u, int n, 
     r.args.alg = alg & NLS_ALG_MASK;
     r.args.abstol = abstol;
     r.args.maxiters = maxiters;
+    r.args.budget_ns = (unsigned long long)h->opt.deadline_us * 1000ull;
     if (out) {
         r.args.status = out->status;
         r.args.iters = out->iters;
@@ -946,6 +948,10 @@ int nls_set_option(nls_handle h, int option, int64_t value)
         h->opt.refill_below = (int)value;
         return NLS_OK;
     case NLS_OPT_GRAPH: h->opt.graph = value != 0; return NLS_OK;
+    case NLS_OPT_DEADLINE_US:
+        if (value < 0 || value > (int64_t)1 << 40) return fail(h, NLS_E_INVALID, "deadline %lld us out of range", (long long)value);
+        h->opt.deadline_us = value;
+        return NLS_OK;
     case NLS_OPT_CTAS_PER_SM:
         if (value < 0 || value > 64) return fail(h, NLS_E_INVALID, "CTAs per SM %lld outside [0, 64]", (long long)value);
         h->opt.ctas_per_sm = (int)value;

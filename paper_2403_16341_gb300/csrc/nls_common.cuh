@@ -54,7 +54,17 @@ struct SolveArgs {
     // when set, the instance count is min(batch, *dyn_batch), read on the
     // device (a count produced by an earlier kernel of the same stream)
     const unsigned long long *dyn_batch;
+    // > 0: stop iterating once this many nanoseconds of %globaltimer have
+    // passed since the kernel started; unfinished instances end NLS_ABORTED
+    unsigned long long budget_ns;
 };
+
+NLS_DI unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 NLS_DI void apply_dyn_batch(SolveArgs &a)
 {

@@ -46,6 +46,7 @@ struct CtaSmem {
     double rd[CTA_TPB / 32];
     uint64_t rm[CTA_TPB / 32];
     long long inst;
+    int late;
 };
 
 // Adds the factor U in pivot-position order, for the single-warp back
@@ -563,6 +564,7 @@ __global__ void __launch_bounds__(CTA_TPB) k_solve_cta(SolveArgs a)
     s.n = a.n;
     s.B = a.ld;
     s.params = a.params;
+    const unsigned long long t_end = a.budget_ns ? global_ns() + a.budget_ns : ~0ull;
     bool first = true;
     for (;;) {
         if (s.tid == 0) {
@@ -577,7 +579,20 @@ __global__ void __launch_bounds__(CTA_TPB) k_solve_cta(SolveArgs a)
         __syncthreads();
         if (s.k >= a.batch) break;
         s.init(a, sm);
-        while (s.status == ST_RUNNING) s.pass(a, sm);
+        while (s.status == ST_RUNNING) {
+            if (a.budget_ns) {
+                // one clock for the whole CTA: the decision stays uniform
+                if (s.tid == 0) sm.late = global_ns() > t_end;
+                __syncthreads();
+                const bool late = sm.late;
+                __syncthreads();
+                if (late) {
+                    s.status = ST_ABORTED;
+                    break;
+                }
+            }
+            s.pass(a, sm);
+        }
         s.finish(a, sm);
     }
 }

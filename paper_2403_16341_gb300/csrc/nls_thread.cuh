@@ -358,6 +358,7 @@ __global__ void __launch_bounds__(THREAD_TPB) k_solve_thread(SolveArgs a)
     const ParamView pv{sd + lane, sf + lane, THREAD_TPB};
     const unsigned FULL = 0xffffffffu;
 
+    const unsigned long long t_end = a.budget_ns ? global_ns() + a.budget_ns : ~0ull;
     S s;
     bool have = false;     // lane holds a running instance
     bool exhausted = false; // no more work for this warp
@@ -410,7 +411,8 @@ __global__ void __launch_bounds__(THREAD_TPB) k_solve_thread(SolveArgs a)
             continue;
         }
         if (have) {
-            s.pass(pv, a);
+            if (a.budget_ns && global_ns() > t_end) s.status = ST_ABORTED;
+            else s.pass(pv, a);
             if (s.status != ST_RUNNING) {
                 s.finish(a, k);
                 local_solved += (s.status == ST_SUCCESS);

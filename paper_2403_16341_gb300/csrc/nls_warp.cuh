@@ -471,6 +471,7 @@ __global__ void __launch_bounds__(WARP_TPB) k_solve_warp(SolveArgs a)
     SM &sm = reinterpret_cast<SM *>(smem_raw)[warp * SEGS + seg];
     const unsigned FULL = 0xffffffffu;
 
+    const unsigned long long t_end = a.budget_ns ? global_ns() + a.budget_ns : ~0ull;
     S s;
     s.r = lane % L;
     s.n = a.n;
@@ -518,7 +519,14 @@ __global__ void __launch_bounds__(WARP_TPB) k_solve_warp(SolveArgs a)
             if (exhausted) break;
             continue;
         }
-        s.pass(a, sm, have);
+        // the deadline test is warp-uniform (lane 0's clock), so skipping the
+        // pass never splits a collective
+        const bool late = a.budget_ns && __shfl_sync(FULL, global_ns(), 0) > t_end;
+        if (late) {
+            if (have) s.status = ST_ABORTED;
+        } else {
+            s.pass(a, sm, have);
+        }
         if (have && s.status != ST_RUNNING) {
             s.finish(a, k);
             local_solved += (s.status == ST_SUCCESS && s.r == 0);
