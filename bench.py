@@ -582,6 +582,59 @@ def run_workload(args, local):
         line["config"] = "open-loop Poisson arrivals, config-3 request mix"
         for name, alg in (("mixed", LS | MIXED), ("fp64", LS), ("mixed_again", LS | MIXED)):
             res[name] = run_serving(args, nls, local, alg=alg)
+    elif args.workload == "adjoint":
+        # sensitivities of 2^20 cubic n = 8 roots: dL/d(A, b) for cotangents w
+        b = I.workload_cubic_n8()
+        dbs = _device_batches(torch, [b], dev)
+        _, p, u0, u, outs = dbs[0]
+        u.copy_(u0)
+        solver.wait(solver.submit(b.family, p, u, LS | MIXED, ABSTOL, MAXITERS, outs))
+        w = torch.randn_like(u0)
+        grad = torch.empty_like(p)
+        st = torch.empty(b.batch, dtype=torch.int32, device=dev)
+        times = []
+        for r in range(max(args.warmup, 3) + args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            nls.nls_adjoint(solver.h, b.family, p.data_ptr(), u.data_ptr(), N_SYS, b.batch,
+                            w.data_ptr(), grad.data_ptr(), st.data_ptr())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r >= max(args.warmup, 3):
+                times.append(e0.elapsed_time(e1))
+        ms = float(np.median(times))
+        bytes_moved = b.batch * 8 * (b.params.shape[0] * 2 + 2 * N_SYS) + b.batch * 4
+        line["config"] = "adjoint sensitivities of 2^20 cubic n=8 roots (FP64, one instance per thread)"
+        res["adjoint"] = {"ms": ms, "instances_per_s": b.batch / (ms / 1e3),
+                          "hbm_gbs": bytes_moved / (ms / 1e3) / 1e9,
+                          "singular": int((st != 0).sum().item())}
+    elif args.workload == "poly":
+        # Rosenbrock n = 8 from the Sec. 3.4 starts, every third moved to the
+        # Fig. 1 start where plain Newton fails
+        b = I.rosenbrock_batch(8, 1 << 18, seed=0)
+        b.u0[0, ::3] = -1.2
+        b.u0[1:, ::3] = 1.0
+        dbs = _device_batches(torch, [b], dev)
+        line["config"] = ("2^18 generalized Rosenbrock n=8, u0 ~ U[0,1)^8 with every third "
+                          "at (-1.2, 1, ..., 1); maxiters 300")
+        for name, alg in (("newton", NEWTON), ("poly", 3), ("poly_mixed", 3 | MIXED)):
+            times, solved = [], 0
+            for r in range(max(args.warmup, 3) + args.steps):
+                _, p, u0, u, outs = dbs[0]
+                u.copy_(u0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                q = solver.submit(b.family, None, u, alg, ABSTOL, 300, outs)
+                solver.flush()
+                e1.record(stream)
+                sv = solver.wait(q)
+                torch.cuda.synchronize()
+                if r >= max(args.warmup, 3):
+                    times.append(e0.elapsed_time(e1))
+                    solved = sv
+            ms = float(np.median(times))
+            res[name] = {"ms": ms, "solved": solved, "solved_fraction": solved / b.batch,
+                         "solved_per_s": solved / (ms / 1e3)}
     elif args.workload == "bratu-large":
         batches = I.workload_bratu_large()
         dbs = _device_batches(torch, batches, dev)
@@ -617,7 +670,8 @@ def main():
     ap.add_argument("--no-persistent", action="store_true",
                     help="one-block-per-chunk grids instead of persistent ones (comparison runs)")
     ap.add_argument("--workload", default="cubic8",
-                    choices=["cubic8", "cubic3", "uneven", "bratu-large", "serving"],
+                    choices=["cubic8", "cubic3", "uneven", "bratu-large", "serving", "adjoint",
+                             "poly"],
                     help="cubic8: the benchmark step; the others print their own JSON line")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-Newton bar, the end-to-end leg and the CPU baseline")
