@@ -609,7 +609,7 @@ def run_workload(args, local):
                           "hbm_gbs": bytes_moved / (ms / 1e3) / 1e9,
                           "singular": int((st != 0).sum().item())}
     elif args.workload == "poly":
-        # Rosenbrock n = 8 from the Sec. 3.4 starts, every third moved to the
+        # Rosenbrock n = 8 from the Sec. 3.3 starts, every third moved to the
         # Fig. 1 start where plain Newton fails
         b = I.rosenbrock_batch(8, 1 << 18, seed=0)
         b.u0[0, ::3] = -1.2

@@ -12,7 +12,7 @@
  * numbers (Sec. 2.4) or from the family's analytic formula, and each Newton
  * system is solved with a dense LU with partial pivoting (Sec. 3.2, Fig. 5).
  * An instance has converged when ||F(u_k)||_inf <= abstol (Sec. 2.1).  The
- * paper's own GPU form of this path is Sec. 3.4: statically sized,
+ * paper's own GPU form of this path is Sec. 3.3: statically sized,
  * non-allocating solvers, one instance per GPU thread.
  *
  * Conventions for every call:

@@ -20,6 +20,12 @@
  *                        Powell's dogleg
  *   Sec. 3.2 (Fig. 5)    small dense systems use a native LU (partial pivoting)
  *   Sec. 2.2.1, Eq. 5    generalized Rosenbrock function
+ *   Sec. 2.1, Eq. 3      Halley: a = Newton step, J b = H a a,
+ *                        du = (a o a) / (a + b/2) elementwise
+ *   Sec. 2.1, Eq. 4      Potra-Ptak: two solves with the same J_k,
+ *                        y = u + du1, u_{k+1} = y + du2 with J_k du2 = -f(y)
+ *   Sec. 3.1, Tab. 1     Broyden (identity start) and modified Broyden
+ *                        (true Jacobian start), "good Broyden" update
  *
  * Readings where the paper gives no value (all listed in the design notes):
  *   backtracking c1 = 1e-4, rho = 1/2, at most 30 trials;
@@ -30,6 +36,10 @@
  *   an exactly zero or non-finite pivot is SINGULAR; the iteration count k
  *   counts loop passes (Jacobian uses, including rejected trust-region
  *   passes); Bratu's 1/h^2 is the exact integer (n+1)^2.
+ *   Halley: where a_i + b_i/2 is exactly zero the component of the step is
+ *   a_i (the Newton component).  Potra-Ptak: both substeps are taken in
+ *   every pass, the convergence test is on f(u_{k+1}).  Broyden: full steps,
+ *   no re-initialisation, the update is skipped for a zero step.
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no fast-math, no FMA
  * contraction, so every operation is one IEEE double rounding).
@@ -39,7 +49,8 @@
 #include <string.h>
 
 enum { FAM_CUBIC = 0, FAM_BRATU = 1, FAM_SQUARE = 2, FAM_ROSENBROCK = 3 };
-enum { ALG_NEWTON = 0, ALG_NEWTON_BACKTRACK = 1, ALG_TRUST_DOGLEG = 2 };
+enum { ALG_NEWTON = 0, ALG_NEWTON_BACKTRACK = 1, ALG_TRUST_DOGLEG = 2, ALG_POTRA_PTAK = 4,
+       ALG_HALLEY = 5, ALG_BROYDEN = 6, ALG_MOD_BROYDEN = 7 };
 enum { ST_SUCCESS = 0, ST_MAXITERS = 1, ST_SINGULAR = 2, ST_NONFINITE = 3,
        ST_LS_FAILED = 4, ST_TR_STALLED = 5 };
 
@@ -128,6 +139,31 @@ void oracle_jacobian(int family, int n, const double *p, const double *u, double
             J[i * n + i] = 10.0;
             J[i * n + i - 1] = -20.0 * u[i - 1];
         }
+    }
+}
+
+/* Second directional derivative h = d^2/dt^2 F(u + t a) at t = 0, i.e. the
+ * term H a a of Halley's method (Sec. 2.1, Eq. 3), from the closed-form
+ * second derivatives of each family. */
+void oracle_hvv(int family, int n, const double *p, const double *u, const double *a, double *h)
+{
+    int i;
+    if (family == FAM_CUBIC) {
+        /* the A u and b terms are linear; (u_i + t a_i)^3 gives 6 u_i a_i^2 */
+        for (i = 0; i < n; i++)
+            h[i] = 6.0 * u[i] * a[i] * a[i];
+    } else if (family == FAM_BRATU) {
+        /* the stencil is linear; lambda exp(u_i + t a_i) gives lambda exp(u_i) a_i^2 */
+        for (i = 0; i < n; i++)
+            h[i] = p[0] * exp(u[i]) * a[i] * a[i];
+    } else if (family == FAM_SQUARE) {
+        for (i = 0; i < n; i++)
+            h[i] = 2.0 * a[i] * a[i];
+    } else {
+        /* F_1 is linear; -10 (u_{i-1} + t a_{i-1})^2 gives -20 a_{i-1}^2 */
+        h[0] = 0.0;
+        for (i = 1; i < n; i++)
+            h[i] = -20.0 * a[i - 1] * a[i - 1];
     }
 }
 
@@ -287,6 +323,28 @@ int oracle_dogleg(int n, const double *J, const double *F, const double *dN, dou
     return 2;
 }
 
+/* ---------------------------------------------------------------- Broyden */
+
+/* "Good" Broyden rank-one update of a Jacobian approximation B (row-major):
+ *     B <- B + (df - B du) du^T / (du^T du),
+ * the least change (Frobenius norm) that satisfies the secant condition
+ * B du = df.  No change when du is zero. */
+void oracle_broyden_update(int n, double *B, const double *du, const double *df)
+{
+    int i, j;
+    double dd = dot(n, du, du);
+    double *r;
+    if (!(dd != 0.0)) return;
+    r = malloc(sizeof(double) * (size_t)n);
+    matvec(n, B, du, r);
+    for (i = 0; i < n; i++)
+        r[i] = df[i] - r[i];
+    for (i = 0; i < n; i++)
+        for (j = 0; j < n; j++)
+            B[i * n + j] += r[i] * du[j] / dd;
+    free(r);
+}
+
 /* ---------------------------------------------------------------- solver */
 
 typedef struct {
@@ -309,10 +367,10 @@ static void solve_one(int family, int n, const double *p, double *u, int alg, do
                       int maxiters, oracle_result *res, const oracle_trace *tr)
 {
     size_t nn = (size_t)n * (size_t)n;
-    double *J = malloc(sizeof(double) * (2 * nn + 7 * (size_t)n));
-    double *LU = J + nn;
-    double *F = LU + nn, *dN = F + n, *ut = dN + n, *Ft = ut + n, *Jd = Ft + n, *d = Jd + n,
-           *rhs = d + n;
+    double *J = malloc(sizeof(double) * (3 * nn + 9 * (size_t)n));
+    double *LU = J + nn, *B = LU + nn;
+    double *F = B + nn, *dN = F + n, *ut = dN + n, *Ft = ut + n, *Jd = Ft + n, *d = Jd + n,
+           *rhs = d + n, *h = rhs + n, *bv = h + n;
     int *piv = malloc(sizeof(int) * (size_t)n);
     int i, k = 0, status = ST_MAXITERS, nfev = 0, need_jac = 1, rejections = 0;
     double Delta = TR_DELTA0;
@@ -328,9 +386,40 @@ static void solve_one(int family, int n, const double *p, double *u, int alg, do
         status = ST_SUCCESS;
         goto done;
     }
+    if (alg == ALG_BROYDEN || alg == ALG_MOD_BROYDEN) {
+        /* starting approximation (Tab. 1): the identity, or the true Jacobian */
+        if (alg == ALG_MOD_BROYDEN) {
+            oracle_jacobian(family, n, p, u, B);
+        } else {
+            memset(B, 0, sizeof(double) * nn);
+            for (i = 0; i < n; i++)
+                B[i * n + i] = 1.0;
+        }
+    }
     while (k < maxiters) {
         k++;
-        if (need_jac) {
+        if (alg == ALG_BROYDEN || alg == ALG_MOD_BROYDEN) {
+            /* quasi-Newton step B du = -F, full step, then the good Broyden
+             * update with du and df = F(u + du) - F(u) */
+            memcpy(LU, B, sizeof(double) * nn);
+            if (oracle_lu_factor(n, LU, piv) != 0) {
+                status = ST_SINGULAR;
+                goto done;
+            }
+            for (i = 0; i < n; i++)
+                rhs[i] = -F[i];
+            oracle_lu_solve(n, LU, piv, rhs, d);
+            for (i = 0; i < n; i++)
+                ut[i] = u[i] + d[i];
+            oracle_residual(family, n, p, ut, Ft);
+            nfev++;
+            for (i = 0; i < n; i++)
+                h[i] = Ft[i] - F[i];
+            oracle_broyden_update(n, B, d, h);
+            memcpy(u, ut, sizeof(double) * (size_t)n);
+            memcpy(F, Ft, sizeof(double) * (size_t)n);
+            if (tr) { tr->alpha[k - 1] = 1.0; tr->trials[k - 1] = 1; }
+        } else if (need_jac) {
             /* J_k and the Newton direction J_k dN = -F (Eq. 2) */
             oracle_jacobian(family, n, p, u, J);
             memcpy(LU, J, sizeof(double) * nn);
@@ -342,7 +431,9 @@ static void solve_one(int family, int n, const double *p, double *u, int alg, do
                 rhs[i] = -F[i];
             oracle_lu_solve(n, LU, piv, rhs, dN);
         }
-        if (alg == ALG_NEWTON) {
+        if (alg == ALG_BROYDEN || alg == ALG_MOD_BROYDEN) {
+            /* step taken above */
+        } else if (alg == ALG_NEWTON) {
             for (i = 0; i < n; i++)
                 u[i] = u[i] + dN[i];
             oracle_residual(family, n, p, u, F);
@@ -374,6 +465,34 @@ static void solve_one(int family, int n, const double *p, double *u, int alg, do
             }
             memcpy(u, ut, sizeof(double) * (size_t)n);
             memcpy(F, Ft, sizeof(double) * (size_t)n);
+        } else if (alg == ALG_POTRA_PTAK) {
+            /* Eq. 4: y = u + dN, then J_k du2 = -f(y) with the same factors,
+             * u_{k+1} = y + du2 */
+            for (i = 0; i < n; i++)
+                ut[i] = u[i] + dN[i];
+            oracle_residual(family, n, p, ut, Ft);
+            nfev++;
+            for (i = 0; i < n; i++)
+                rhs[i] = -Ft[i];
+            oracle_lu_solve(n, LU, piv, rhs, d);
+            for (i = 0; i < n; i++)
+                u[i] = ut[i] + d[i];
+            oracle_residual(family, n, p, u, F);
+            nfev++;
+            if (tr) { tr->alpha[k - 1] = 1.0; tr->trials[k - 1] = 1; }
+        } else if (alg == ALG_HALLEY) {
+            /* Eq. 3: a = dN, J_k b = H_k a a, du = (a o a) / (a + b/2) */
+            oracle_hvv(family, n, p, u, dN, h);
+            oracle_lu_solve(n, LU, piv, h, bv);
+            for (i = 0; i < n; i++) {
+                double den = dN[i] + 0.5 * bv[i];
+                d[i] = (den != 0.0) ? (dN[i] * dN[i]) / den : dN[i];
+            }
+            for (i = 0; i < n; i++)
+                u[i] = u[i] + d[i];
+            oracle_residual(family, n, p, u, F);
+            nfev++;
+            if (tr) { tr->alpha[k - 1] = 1.0; tr->trials[k - 1] = 1; }
         } else {
             /* trust region with the dogleg step (Eq. 12-14) */
             double fF, ared, pred, rho;

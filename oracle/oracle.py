@@ -18,6 +18,7 @@ from concurrent.futures import ThreadPoolExecutor
 import numpy as np
 
 ALG_NEWTON, ALG_NEWTON_BACKTRACK, ALG_TRUST_DOGLEG = 0, 1, 2
+ALG_POTRA_PTAK, ALG_HALLEY, ALG_BROYDEN, ALG_MOD_BROYDEN = 4, 5, 6, 7
 ST_SUCCESS, ST_MAXITERS, ST_SINGULAR, ST_NONFINITE, ST_LS_FAILED, ST_TR_STALLED = range(6)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -65,6 +66,8 @@ def _load():
             lib.oracle_polish.restype = ctypes.c_double
             lib.oracle_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
             lib.oracle_adjoint.restype = ctypes.c_int
+            lib.oracle_hvv.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
+            lib.oracle_broyden_update.argtypes = [ctypes.c_int, _D, _D, _D]
             lib.oracle_n_params.argtypes = [ctypes.c_int, ctypes.c_int]
             lib.oracle_n_params.restype = ctypes.c_int
             _lib = lib
@@ -95,6 +98,23 @@ def jacobian(family: int, p, u) -> np.ndarray:
     J = np.empty((u.size, u.size))
     _load().oracle_jacobian(family, u.size, _dp(p), _dp(u), _dp(J))
     return J
+
+
+def hvv(family: int, p, u, a) -> np.ndarray:
+    """d^2/dt^2 F(u + t a) at t = 0 (the H a a term of Halley's method)."""
+    p = _f64(p) if np.size(p) else np.zeros(1)
+    u, a = _f64(u), _f64(a)
+    h = np.empty_like(u)
+    _load().oracle_hvv(family, u.size, _dp(p), _dp(u), _dp(a), _dp(h))
+    return h
+
+
+def broyden_update(B, du, df) -> np.ndarray:
+    """Good Broyden rank-one update of the Jacobian approximation B."""
+    B = _f64(B).copy()
+    du, df = _f64(du), _f64(df)
+    _load().oracle_broyden_update(du.size, _dp(B), _dp(du), _dp(df))
+    return B
 
 
 def lu_factor(A):

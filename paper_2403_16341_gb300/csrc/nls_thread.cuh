@@ -1,6 +1,6 @@
 // nls_thread.cuh -- one instance per GPU thread, for n <= 8 (compile-time N).
 //
-// The paper's GPU path (Sec. 3.4) runs one statically sized, non-allocating
+// The paper's GPU path (Sec. 3.3) runs one statically sized, non-allocating
 // solver per GPU thread.  Here each lane of a warp owns an instance slot and
 // keeps its state in registers: u and F in FP64, the Jacobian and its LU in
 // FP64 or (NLS_MIXED) FP32.  Parameters are staged once per instance into the

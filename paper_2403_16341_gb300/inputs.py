@@ -29,7 +29,7 @@ instances the parameters are a float64 array ``params[E, B]`` with
 The workloads (``workload_*``) reproduce the synthetic families used to
 measure the batched solver: the dense cubic with A = 3 I + G, G ~ N(0, 0.3^2),
 the 1-D Bratu problem with lambda ~ U[0.5, 3], the generalized Rosenbrock
-problem of Sec. 3.4 and an uneven mix of sizes 2..32.
+problem of Sec. 3.3 and an uneven mix of sizes 2..32.
 """
 from __future__ import annotations
 
@@ -210,7 +210,7 @@ def square_batch(n: int, B: int, seed: int = 0, config_id: int = 90,
 
 
 def rosenbrock_batch(n: int, B: int, seed: int = 0, config_id: int = 91) -> Batch:
-    """u0 ~ U[0, 1]^n per instance, as in the Sec. 3.4 GPU example."""
+    """u0 ~ U[0, 1]^n per instance, as in the Sec. 3.3 GPU example."""
     keys = stream_keys(seed, config_id, np.arange(B))
     u0 = uniforms(keys, 0, n)
     return Batch(FAMILY_ROSENBROCK, n, np.zeros((0, B)), np.ascontiguousarray(u0.T))

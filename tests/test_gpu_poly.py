@@ -70,7 +70,7 @@ def test_poly_equals_newton_when_newton_converges(solver):
 
 @pytest.mark.parametrize("n,floor", [(12, 1.0), (40, 0.6)])
 def test_poly_warp_and_cta_tilings(solver, n, floor):
-    # the Sec. 3.4 starts U[0, 1)^n, every third one moved to the Fig. 1 start
+    # the Sec. 3.3 starts U[0, 1)^n, every third one moved to the Fig. 1 start
     # (-1.2, 1, ..., 1) where plain Newton fails; the oracle composition solves
     # all of them at n = 12 and 199 of 301 at n = 40 within 300 passes
     b = I.rosenbrock_batch(n, 301, seed=n)

@@ -148,7 +148,7 @@ def test_rosenbrock_fig1_example():
 
 
 def test_rosenbrock_gpu_example_inputs():
-    # Sec. 3.4: u0 ~ U[0, 1)^10, plain Newton; root is the all-ones vector
+    # Sec. 3.3: u0 ~ U[0, 1)^10, plain Newton; root is the all-ones vector
     b = I.rosenbrock_batch(10, 256)
     u, st, it, r, _ = O.solve_batch(ROSEN, b.params, b.u0, O.ALG_NEWTON, 1e-8, 1000)
     ok = st == O.ST_SUCCESS
