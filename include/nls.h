@@ -54,12 +54,27 @@ enum nls_alg {
     NLS_NEWTON = 0,           /* Sec. 2.1, Eq. 2                               */
     NLS_NEWTON_BACKTRACK = 1, /* Sec. 2.2.1: Armijo (Eq. 8-9), alpha <- alpha/2 */
     NLS_TRUST_DOGLEG = 2,     /* Sec. 2.2.2: Eq. 12-14, Powell's dogleg          */
-    NLS_POLYALG = 3           /* Sec. 3.2 poly-algorithm for n <= 25 (no quasi-
+    NLS_POLYALG = 3,          /* Sec. 3.2 poly-algorithm for n <= 25 (no quasi-
                                  Newton stage): Newton on every instance; the
                                  ones that fail restart from u0 with
                                  backtracking, then with the trust region.
                                  iters = the final stage's passes, nfev = all
                                  stages' residual evaluations.                */
+    /* The following run one instance per thread only: n <= 8, no
+       NLS_ANALYTIC_JAC, no NLS_TILE_WARP / NLS_TILE_CTA (NLS_E_UNSUPPORTED). */
+    NLS_POTRA_PTAK = 4,       /* Sec. 2.1, Eq. 4: y = u + du1, u' = y + du2 with
+                                 J(u) du1 = -F(u), J(u) du2 = -F(y) (one
+                                 Jacobian and LU, two residuals per pass)     */
+    NLS_HALLEY = 5,           /* Sec. 2.1, Eq. 3: a = -J^-1 F, J b = H a a
+                                 (second directional derivative by forward-
+                                 mode jets), step (a o a) / (a + b/2)
+                                 elementwise; a_i where a_i + b_i/2 == 0      */
+    NLS_BROYDEN = 6,          /* Sec. 3.1, Tab. 1: quasi-Newton, B_0 = I, good
+                                 Broyden update after each full step; kept as
+                                 B^-1 (Sherman-Morrison), no Jacobian, no LU.
+                                 A singular update ends NLS_SINGULAR.         */
+    NLS_MOD_BROYDEN = 7       /* Tab. 1 "Mod. Broyden": as NLS_BROYDEN with
+                                 B_0 = J(u_0) by forward mode                  */
 };
 #define NLS_ALG_MASK 0xff
 enum nls_flags {

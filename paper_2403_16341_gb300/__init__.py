@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libnls.so")
 NLS_CUBIC, NLS_BRATU, NLS_SQUARE, NLS_ROSENBROCK = 0, 1, 2, 3
 # nls_alg and flags
 NLS_NEWTON, NLS_NEWTON_BACKTRACK, NLS_TRUST_DOGLEG, NLS_POLYALG = 0, 1, 2, 3
+NLS_POTRA_PTAK, NLS_HALLEY, NLS_BROYDEN, NLS_MOD_BROYDEN = 4, 5, 6, 7
 NLS_ALG_MASK = 0xFF
 NLS_MIXED = 1 << 8
 NLS_ANALYTIC_JAC = 1 << 9

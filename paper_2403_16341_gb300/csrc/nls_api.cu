@@ -38,6 +38,30 @@ KernelInfo thread_kernel(int family, int n, bool mixed, bool analytic)
     default: return KernelInfo{};
     }
 }
+#define NLS_EXT_DECL(alg)                                  \
+    KernelInfo thread_##alg##_cubic(int n, bool mixed);    \
+    KernelInfo thread_##alg##_bratu(int n, bool mixed);    \
+    KernelInfo thread_##alg##_square(int n, bool mixed);   \
+    KernelInfo thread_##alg##_rosenbrock(int n, bool mixed);
+NLS_EXT_DECL(potra_ptak)
+NLS_EXT_DECL(halley)
+NLS_EXT_DECL(broyden)
+#undef NLS_EXT_DECL
+
+// Potra-Ptak, Halley, Broyden and modified Broyden: one instance per thread.
+KernelInfo thread_ext_kernel(int family, int n, int alg, bool mixed)
+{
+    using Fn = KernelInfo (*)(int, bool);
+    static const Fn table[3][4] = {
+        {thread_potra_ptak_cubic, thread_potra_ptak_bratu, thread_potra_ptak_square, thread_potra_ptak_rosenbrock},
+        {thread_halley_cubic, thread_halley_bratu, thread_halley_square, thread_halley_rosenbrock},
+        {thread_broyden_cubic, thread_broyden_bratu, thread_broyden_square, thread_broyden_rosenbrock}};
+    const int row = alg == ALG_POTRA_PTAK ? 0 : alg == ALG_HALLEY ? 1
+                    : (alg == ALG_BROYDEN || alg == ALG_MOD_BROYDEN) ? 2 : -1;
+    if (row < 0 || family < FAM_CUBIC || family > FAM_ROSENBROCK) return KernelInfo{};
+    return table[row][family](n, mixed);
+}
+
 KernelInfo warp_kernel_fp64(int family, int L);
 KernelInfo warp_kernel_mixed(int family, int L);
 
@@ -214,8 +238,21 @@ static int select_kernel(nls_batch *h, int family, int n, int alg, KernelInfo *o
             rate = it->second.rate;
         }
     }
-    if (!tiles) tiles = n <= 8 ? NLS_TILE_THREAD : n <= 32 ? NLS_TILE_WARP : NLS_TILE_CTA;
-    if (tiles == NLS_TILE_THREAD) {
+    if ((alg & NLS_ALG_MASK) >= NLS_POTRA_PTAK) {
+        if (tiles && tiles != NLS_TILE_THREAD)
+            return fail(h, NLS_E_UNSUPPORTED, "algorithm %d runs one instance per thread only", alg & NLS_ALG_MASK);
+        if (analytic)
+            return fail(h, NLS_E_UNSUPPORTED, "algorithm %d takes derivatives by forward mode only",
+                        alg & NLS_ALG_MASK);
+        if (n > 8) return fail(h, NLS_E_UNSUPPORTED, "algorithm %d holds n <= 8 (n = %d)", alg & NLS_ALG_MASK, n);
+        tiles = NLS_TILE_THREAD;
+        *out = nls::thread_ext_kernel(family, n, alg & NLS_ALG_MASK, mixed);
+    } else {
+        if (!tiles) tiles = n <= 8 ? NLS_TILE_THREAD : n <= 32 ? NLS_TILE_WARP : NLS_TILE_CTA;
+    }
+    if ((alg & NLS_ALG_MASK) >= NLS_POTRA_PTAK) {
+        // kernel chosen above
+    } else if (tiles == NLS_TILE_THREAD) {
         if (n > 8) return fail(h, NLS_E_UNSUPPORTED, "thread tiling holds n <= 8 (n = %d)", n);
         *out = thread_kernel(family, n, mixed, analytic);
     } else if (tiles == NLS_TILE_WARP) {
@@ -562,7 +599,7 @@ static int validate(nls_batch *h, int family, const double *params, const double
     if (maxiters < 0) return fail(h, NLS_E_INVALID, "negative maxiters");
     if (!(abstol >= 0.0) || !std::isfinite(abstol)) return fail(h, NLS_E_INVALID, "abstol must be finite and >= 0");
     const int a = alg & NLS_ALG_MASK;
-    if (a > NLS_POLYALG) return fail(h, NLS_E_INVALID, "unknown algorithm %d", a);
+    if (a > NLS_MOD_BROYDEN) return fail(h, NLS_E_INVALID, "unknown algorithm %d", a);
     if (alg & ~(NLS_ALG_MASK | NLS_MIXED | NLS_ANALYTIC_JAC | NLS_TILE_THREAD | NLS_TILE_WARP | NLS_TILE_CTA))
         return fail(h, NLS_E_INVALID, "unknown flags in alg 0x%x", alg);
     if (batch > 0 && !u) return fail(h, NLS_E_INVALID, "u is NULL");
@@ -820,6 +857,9 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
         return fail(h, NLS_E_INVALID, "nls_autotune chooses the tiling: pass no tiling flag");
     if ((alg & NLS_ALG_MASK) == NLS_POLYALG)
         return fail(h, NLS_E_INVALID, "tune the stage algorithms, not NLS_POLYALG");
+    if ((alg & NLS_ALG_MASK) >= NLS_POTRA_PTAK && ((alg & NLS_ANALYTIC_JAC) || n > 8))
+        return fail(h, NLS_E_UNSUPPORTED, "algorithm %d: one instance per thread (n <= 8), forward-mode derivatives",
+                    alg & NLS_ALG_MASK);
     NLS_CUDA(h, cudaSetDevice(h->device));
     rc = flush_pending(h);
     if (rc) return rc;
@@ -850,11 +890,15 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
         t.refill = refill;
         cands.push_back(t);
     };
-    if (n <= 8) {
+    const bool ext = (alg & NLS_ALG_MASK) >= NLS_POTRA_PTAK;
+    if (ext) {
+        for (int r : {REFILL_STATIC, 0, 16, 24, 31}) add(NLS_TILE_THREAD, 0, r);
+    } else if (n <= 8) {
         for (int r : {REFILL_STATIC, 0, 16, 24, 31}) add(NLS_TILE_THREAD, 0, r);
         for (int r : {REFILL_STATIC, -1}) add(NLS_TILE_WARP, 8, r);
     }
     for (int r : {REFILL_STATIC, -1}) {
+        if (ext) break;
         if (n <= 16) add(NLS_TILE_WARP, 16, r);
         if (n <= 32) add(NLS_TILE_WARP, 32, r);
         if (n > 8) add(NLS_TILE_CTA, 0, r);
@@ -869,7 +913,8 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
     base.maxiters = maxiters;
     Tuned best;
     for (Tuned &c : cands) {
-        KernelInfo k = c.tiles == NLS_TILE_THREAD ? thread_kernel(family, n, mixed, analytic)
+        KernelInfo k = ext ? nls::thread_ext_kernel(family, n, alg & NLS_ALG_MASK, mixed)
+                       : c.tiles == NLS_TILE_THREAD ? thread_kernel(family, n, mixed, analytic)
                        : c.tiles == NLS_TILE_WARP ? warp_kernel(family, n, mixed, c.lanes)
                                                   : cta_kernel(family, n, mixed);
         if (!k.launch) continue;

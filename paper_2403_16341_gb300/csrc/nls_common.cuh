@@ -10,7 +10,15 @@
 namespace nls {
 
 enum : int { FAM_CUBIC = 0, FAM_BRATU = 1, FAM_SQUARE = 2, FAM_ROSENBROCK = 3 };
-enum : int { ALG_NEWTON = 0, ALG_NEWTON_BACKTRACK = 1, ALG_TRUST_DOGLEG = 2 };
+enum : int {
+    ALG_NEWTON = 0,
+    ALG_NEWTON_BACKTRACK = 1,
+    ALG_TRUST_DOGLEG = 2,
+    ALG_POTRA_PTAK = 4,
+    ALG_HALLEY = 5,
+    ALG_BROYDEN = 6,
+    ALG_MOD_BROYDEN = 7
+};
 enum : int {
     ST_RUNNING = -1,
     ST_SUCCESS = 0,
@@ -145,6 +153,16 @@ struct SeedVec {
     const T *x;
     template <int J>
     NLS_DI Dual<N, (1u << J), T> get() const { return seed<N, J, T>(x[J]); }
+};
+
+// Jets along the direction a at the point x (second directional derivative).
+template <int N, class T>
+struct JetVec {
+    using scalar = T;
+    const T *x;
+    const T *a;
+    template <int J>
+    NLS_DI Jet<T, false> get() const { return Jet<T, false>{x[J], a[J], T(0)}; }
 };
 
 // ---------------------------------------------------------------------------

@@ -139,4 +139,107 @@ NLS_DI Dual<N, A, T> exp(const Dual<N, A, T> &x)
 NLS_DI double exp(double x) { return nls_exp(x); }
 NLS_DI float exp(float x) { return nls_exp(x); }
 
+// ---------------------------------------------------------------------------
+// Second-order Taylor numbers along one direction a: evaluated on
+// x(t) = u + t a, a Jet carries x(0), x'(0) and x''(0), so a residual row
+// evaluated on jets yields d^2/dt^2 F_i(u + t a) at t = 0 = (H a a)_i, the
+// term Halley's method (Sec. 2.1, Eq. 3) needs, by forward mode and without
+// forming the n x n x n second derivative.  S2 = false marks, at compile
+// time, a jet whose second derivative is structurally zero (the seeds and
+// everything linear in them), so linear parts of a residual cost two
+// operations per term instead of three.
+template <class T, bool S2>
+struct Jet {
+    T v, d1, d2;
+};
+
+template <class T, bool A, bool B>
+NLS_DI Jet<T, A || B> operator+(const Jet<T, A> &x, const Jet<T, B> &y)
+{
+    Jet<T, A || B> r;
+    r.v = x.v + y.v;
+    r.d1 = x.d1 + y.d1;
+    if constexpr (A && B) r.d2 = x.d2 + y.d2;
+    else if constexpr (A) r.d2 = x.d2;
+    else if constexpr (B) r.d2 = y.d2;
+    else r.d2 = T(0);
+    return r;
+}
+
+template <class T, bool A, bool B>
+NLS_DI Jet<T, A || B> operator-(const Jet<T, A> &x, const Jet<T, B> &y)
+{
+    Jet<T, A || B> r;
+    r.v = x.v - y.v;
+    r.d1 = x.d1 - y.d1;
+    if constexpr (A && B) r.d2 = x.d2 - y.d2;
+    else if constexpr (A) r.d2 = x.d2;
+    else if constexpr (B) r.d2 = -y.d2;
+    else r.d2 = T(0);
+    return r;
+}
+
+// (x y)'' = x'' y + 2 x' y' + x y''
+template <class T, bool A, bool B>
+NLS_DI Jet<T, true> operator*(const Jet<T, A> &x, const Jet<T, B> &y)
+{
+    Jet<T, true> r;
+    r.v = x.v * y.v;
+    r.d1 = x.d1 * y.v + x.v * y.d1;
+    T s = T(2) * x.d1 * y.d1;
+    if constexpr (A) s = s + x.d2 * y.v;
+    if constexpr (B) s = s + x.v * y.d2;
+    r.d2 = s;
+    return r;
+}
+
+template <class T, bool A>
+NLS_DI Jet<T, A> operator*(T c, const Jet<T, A> &x)
+{
+    Jet<T, A> r;
+    r.v = c * x.v;
+    r.d1 = c * x.d1;
+    r.d2 = A ? c * x.d2 : T(0);
+    return r;
+}
+
+template <class T, bool A>
+NLS_DI Jet<T, A> operator+(const Jet<T, A> &x, T c)
+{
+    Jet<T, A> r = x;
+    r.v = x.v + c;
+    return r;
+}
+
+template <class T, bool A>
+NLS_DI Jet<T, A> operator-(const Jet<T, A> &x, T c)
+{
+    Jet<T, A> r = x;
+    r.v = x.v - c;
+    return r;
+}
+
+template <class T, bool A>
+NLS_DI Jet<T, A> operator-(T c, const Jet<T, A> &x)
+{
+    Jet<T, A> r;
+    r.v = c - x.v;
+    r.d1 = -x.d1;
+    r.d2 = A ? -x.d2 : T(0);
+    return r;
+}
+
+// (e^x)'' = e^x (x'^2 + x'')
+template <class T, bool A>
+NLS_DI Jet<T, true> exp(const Jet<T, A> &x)
+{
+    Jet<T, true> r;
+    r.v = nls_exp(x.v);
+    r.d1 = r.v * x.d1;
+    T s = x.d1 * x.d1;
+    if constexpr (A) s = s + x.d2;
+    r.d2 = r.v * s;
+    return r;
+}
+
 } // namespace nls

@@ -82,6 +82,79 @@ NLS_DI bool lu_solve(P (&a)[N][N], P (&b)[N])
     return true;
 }
 
+// LU with partial pivoting that keeps its factors for later solves: on
+// return a holds U on and above the diagonal and the multipliers of L below
+// it, piv[k] is the row exchanged with row k at step k (whole rows move, so
+// the stored multipliers follow their rows) and r[k] = 1 / u_kk.  Same pivot
+// choice as lu_solve.  Returns false on a zero / non-finite pivot.
+template <int N, class P>
+NLS_DI bool lu_factor(P (&a)[N][N], int (&piv)[N], P (&r)[N])
+{
+    using K = decltype(mag_bits(P(0)));
+    const K inf = inf_bits(P(0));
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        K best = mag_bits(a[k][k]);
+        int p = k;
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) {
+            K m = mag_bits(a[i][k]);
+            m = (m > inf) ? K(0) : m;
+            if (m > best) { best = m; p = i; }
+        }
+        piv[k] = p;
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) {
+            const bool s = (p == i);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                P t = a[k][j];
+                a[k][j] = s ? a[i][j] : t;
+                a[i][j] = s ? t : a[i][j];
+            }
+        }
+        const K pm = mag_bits(a[k][k]);
+        if (pm == K(0) || pm >= inf) return false;
+        r[k] = rcp(a[k][k]);
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) {
+            const P l = a[i][k] * r[k];
+            a[i][k] = l;
+#pragma unroll
+            for (int j = k + 1; j < N; ++j) a[i][j] -= l * a[k][j];
+        }
+    }
+    return true;
+}
+
+// b <- A^-1 b from the factors of lu_factor: the row exchanges in order,
+// then L y = P b (unit diagonal) and U x = y.
+template <int N, class P>
+NLS_DI void lu_apply(const P (&a)[N][N], const int (&piv)[N], const P (&r)[N], P (&b)[N])
+{
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) {
+            const bool s = (piv[k] == i);
+            P t = b[k];
+            b[k] = s ? b[i] : t;
+            b[i] = s ? t : b[i];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+#pragma unroll
+        for (int i = k + 1; i < N; ++i) b[i] -= a[i][k] * b[k];
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        P s = b[i];
+#pragma unroll
+        for (int j = i + 1; j < N; ++j) s -= a[i][j] * b[j];
+        b[i] = s * r[i];
+    }
+}
+
 template <class R>
 struct mask_of;
 template <int M_N, uint32_t M, class T>
@@ -345,11 +418,14 @@ constexpr int thread_smem_bytes()
     return THREAD_TPB * family_params<FAM>(N) * (8 + (MIXED ? 4 : 0));
 }
 
-template <int N, int FAM, bool MIXED, bool ANALYTIC>
-__global__ void __launch_bounds__(THREAD_TPB) k_solve_thread(SolveArgs a)
+// The lane loop shared by every one-instance-per-thread solver S (S::E
+// parameters, init / pass / finish, a status): each lane owns an instance
+// slot, all lanes of the warp step in lock step, and idle lanes are refilled
+// from the work counter (persistent launches) or from the static slot.
+template <class S, bool MIXED>
+NLS_DI void thread_lanes(SolveArgs &a)
 {
     apply_dyn_batch(a);
-    using S = ThreadSolver<N, FAM, MIXED, ANALYTIC>;
     constexpr int E = S::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double *sd = reinterpret_cast<double *>(smem_raw);
@@ -427,6 +503,12 @@ __global__ void __launch_bounds__(THREAD_TPB) k_solve_thread(SolveArgs a)
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
         if (lane == 0 && t) atomicAdd(a.solved, t);
     }
+}
+
+template <int N, int FAM, bool MIXED, bool ANALYTIC>
+__global__ void __launch_bounds__(THREAD_TPB) k_solve_thread(SolveArgs a)
+{
+    thread_lanes<ThreadSolver<N, FAM, MIXED, ANALYTIC>, MIXED>(a);
 }
 
 } // namespace nls

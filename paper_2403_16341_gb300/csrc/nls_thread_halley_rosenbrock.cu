@@ -1,0 +1,9 @@
+// Thread-tiled Halley solver instantiations for the rosenbrock family (n = 1..8).
+#include "nls_thread_ext.cuh"
+
+namespace nls {
+KernelInfo thread_halley_rosenbrock(int n, bool mixed)
+{
+    return thread_ext_info_family<FAM_ROSENBROCK, ALG_HALLEY>(n, mixed);
+}
+} // namespace nls

@@ -1,0 +1,9 @@
+// Thread-tiled Potra-Ptak solver instantiations for the bratu family (n = 1..8).
+#include "nls_thread_ext.cuh"
+
+namespace nls {
+KernelInfo thread_potra_ptak_bratu(int n, bool mixed)
+{
+    return thread_ext_info_family<FAM_BRATU, ALG_POTRA_PTAK>(n, mixed);
+}
+} // namespace nls

@@ -1,0 +1,9 @@
+// Thread-tiled Potra-Ptak solver instantiations for the rosenbrock family (n = 1..8).
+#include "nls_thread_ext.cuh"
+
+namespace nls {
+KernelInfo thread_potra_ptak_rosenbrock(int n, bool mixed)
+{
+    return thread_ext_info_family<FAM_ROSENBROCK, ALG_POTRA_PTAK>(n, mixed);
+}
+} // namespace nls

@@ -6,7 +6,8 @@ import numpy as np
 
 import oracle as O
 
-ORACLE_ALG = {0: O.ALG_NEWTON, 1: O.ALG_NEWTON_BACKTRACK, 2: O.ALG_TRUST_DOGLEG}
+ORACLE_ALG = {0: O.ALG_NEWTON, 1: O.ALG_NEWTON_BACKTRACK, 2: O.ALG_TRUST_DOGLEG,
+              4: O.ALG_POTRA_PTAK, 5: O.ALG_HALLEY, 6: O.ALG_BROYDEN, 7: O.ALG_MOD_BROYDEN}
 FP64_TOL = 1e-9   # relative to max(1, ||u*||_inf), u* = polished oracle root
 MIXED_TOL = 1e-8
 

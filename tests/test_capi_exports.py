@@ -49,3 +49,15 @@ def test_create_without_gpu_fails_cleanly(lib):
     import paper_2403_16341_gb300 as nls
     with pytest.raises(nls.NlsError):
         nls.nls_batch_create(0)
+
+
+def test_header_enum_values_match_binding():
+    import paper_2403_16341_gb300 as nls
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    found = 0
+    for name, expr in re.findall(r"\b(NLS_[A-Z0-9_]+)\s*=\s*(-?\d+(?:\s*<<\s*\d+)?)", text):
+        a, _, b = expr.partition("<<")
+        value = int(a) << int(b) if b else int(a)
+        assert getattr(nls, name) == value, name
+        found += 1
+    assert found >= 30

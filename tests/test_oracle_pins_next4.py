@@ -294,3 +294,16 @@ def test_bratu_n2_matches_bisection(alg):
     u, st, it, r, _ = O.solve_one(BRATU, [lam], [0.0, 0.0], alg, abstol=1e-13, maxiters=100)
     assert st == O.ST_SUCCESS
     np.testing.assert_allclose(u, [lo, lo], rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- statuses
+
+def test_singular_statuses():
+    # J = diag(2u) = 0 at u0 = 0: the Jacobian methods stop at pass 1
+    for alg in (O.ALG_POTRA_PTAK, O.ALG_HALLEY, O.ALG_MOD_BROYDEN):
+        _, st, it, _, _ = O.solve_one(SQUARE, [2.0, 3.0], [0.0, 0.0], alg)
+        assert st == O.ST_SINGULAR and it == 1
+    # u^2 = 3 from u0 = 3 with B_0 = 1: du = -6 lands on -3 where F = 6 again,
+    # the secant slope df/du is 0, B_1 = 0 exactly and pass 2 finds it singular
+    _, st, it, _, _ = O.solve_one(SQUARE, [3.0], [3.0], O.ALG_BROYDEN)
+    assert st == O.ST_SINGULAR and it == 2
