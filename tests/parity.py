@@ -41,8 +41,11 @@ def check_parity(batch, g, o, mixed, abstol=1e-10, polish=True, chaotic=False):
     chaotic=True is for iterations whose outcome depends on rounding (plain
     Newton on the generalized Rosenbrock function far from its root, where
     two correct FP64 solvers already disagree): statuses are then not
-    compared; instances both sides solve must agree, and every instance the
-    GPU reports solved must satisfy the residual test."""
+    compared; every instance the GPU reports solved must satisfy the FP64
+    residual test, and instances both sides solve must agree -- unless the
+    two landed on different roots (Bratu's two branches, +-sqrt(p)), which
+    is a valid outcome of a rounding-driven iteration: then only most of
+    them must share a root, and those are compared."""
     ok_o = o["status"] == O.ST_SUCCESS
     ok_g = g["status"] == O.ST_SUCCESS
     if chaotic:
@@ -58,6 +61,12 @@ def check_parity(batch, g, o, mixed, abstol=1e-10, polish=True, chaotic=False):
                              else np.zeros((0, both.sum())), ref)
     err = rel_err(g["u"][:, both], ref)
     tol = MIXED_TOL if mixed else FP64_TOL
+    if chaotic and err.size:
+        same = err <= 1e-4  # far beyond any tolerance: another root
+        assert same.mean() >= 0.5
+        err = err[same]
+        both[np.nonzero(both)[0][~same]] = False
+        ref = ref[:, same]
     # Any solver that stops at ||F||_inf <= abstol is only guaranteed
     # ||u - u*||_inf <= ||J(u*)^-1||_inf abstol; where an instance's
     # conditioning makes that bound exceed the gate, the bound (x2) applies.
@@ -71,7 +80,7 @@ def check_parity(batch, g, o, mixed, abstol=1e-10, polish=True, chaotic=False):
     # every successful instance: reported and recomputed FP64 residual <= abstol
     assert (g["resid"][ok_g] <= abstol).all()
     idx = np.nonzero(ok_g)[0]
-    for k in idx[:: max(1, idx.size // 200)]:
+    for k in idx[:: 1 if chaotic else max(1, idx.size // 200)]:
         p = batch.params[:, k] if batch.params.size else np.zeros(1)
         F = O.residual(batch.family, p, g["u"][:, k])
         assert np.abs(F).max() <= abstol

@@ -136,7 +136,7 @@ def test_api_errors(solver):
     cases = [
         (dict(family=9), nls.NLS_E_UNSUPPORTED), (dict(n=0), nls.NLS_E_UNSUPPORTED),
         (dict(n=129), nls.NLS_E_UNSUPPORTED), (dict(batch=-1), nls.NLS_E_INVALID),
-        (dict(alg=7), nls.NLS_E_INVALID), (dict(abstol=-1.0), nls.NLS_E_INVALID),
+        (dict(alg=8), nls.NLS_E_INVALID), (dict(abstol=-1.0), nls.NLS_E_INVALID),
         (dict(abstol=float("nan")), nls.NLS_E_INVALID), (dict(maxiters=-1), nls.NLS_E_INVALID),
         (dict(u=0), nls.NLS_E_INVALID), (dict(params=0), nls.NLS_E_INVALID),
     ]
