@@ -635,6 +635,30 @@ def run_workload(args, local):
             ms = float(np.median(times))
             res[name] = {"ms": ms, "solved": solved, "solved_fraction": solved / b.batch,
                          "solved_per_s": solved / (ms / 1e3)}
+    elif args.workload == "next4":
+        # the higher-order, multi-step and quasi-Newton solvers on the 2^20
+        # cubic n = 8 workload, next to Newton with backtracking
+        b = I.workload_cubic_n8(args.instances)
+        dbs = _device_batches(torch, [b], dev)
+        line["config"] = (f"{b.batch} cubic n=8, A = 3I + G, b ~ U[-5,5]^8, u0 = 0; Halley "
+                          "(Eq. 3), Potra-Ptak (Eq. 4), Broyden / modified Broyden (Tab. 1), one "
+                          "thread per instance, autotuned launch")
+        keep = set(args.variants.split(",")) if args.variants else None
+        _, p, u0, u, outs = dbs[0]
+        for name, alg in (("newton_backtrack", LS), ("halley", 5), ("potra_ptak", 4),
+                          ("mod_broyden", 7), ("broyden", 6)):
+            for prec, m in (("fp64", 0), ("mixed", MIXED)):
+                if keep is not None and f"{name}_{prec}" not in keep:
+                    continue
+                u.copy_(u0)
+                if not args.no_autotune:
+                    solver.autotune(b.family, p, u, alg | m, ABSTOL, MAXITERS)
+                ms, sv, nl = time_flush(torch, solver, dbs, alg | m, args.steps,
+                                        max(args.warmup, 3), stream)
+                it = outs[1][:b.batch].float()
+                res[f"{name}_{prec}"] = {"ms": ms, "solved": sv, "solved_per_s": sv / (ms / 1e3),
+                                         "mean_iters": float(it.mean().item()),
+                                         "launches": nl}
     elif args.workload == "bratu-large":
         batches = I.workload_bratu_large()
         dbs = _device_batches(torch, batches, dev)
@@ -661,7 +685,8 @@ def main():
                     help="instances the CPU oracle solves per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", default="",
-                    help="comma-separated subset of the step's variants (profiling runs)")
+                    help="comma-separated subset of the step's variants, or of the next4 "
+                         "workload's lines (profiling runs)")
     ap.add_argument("--instances", type=int, default=B_FULL,
                     help="batch size (profiling runs; the benchmark uses 2^20)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
@@ -671,13 +696,13 @@ def main():
                     help="one-block-per-chunk grids instead of persistent ones (comparison runs)")
     ap.add_argument("--workload", default="cubic8",
                     choices=["cubic8", "cubic3", "uneven", "bratu-large", "serving", "adjoint",
-                             "poly"],
+                             "poly", "next4"],
                     help="cubic8: the benchmark step; the others print their own JSON line")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-Newton bar, the end-to-end leg and the CPU baseline")
     args = ap.parse_args()
     world, rank, local = dist_env()
-    if args.variants:
+    if args.variants and args.workload == "cubic8":
         keep = set(args.variants.split(","))
         unknown = keep - {v for v, _ in VARIANTS}
         if unknown:

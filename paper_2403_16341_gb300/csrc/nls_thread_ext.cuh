@@ -19,6 +19,11 @@
 //    so a pass costs four n x n matrix-vector products and no
 //    factorisation.  A zero step skips the update; du^T H df = 0 (the
 //    updated B is singular) ends the instance SINGULAR at the next pass.
+//    In FP64, H lives in shared memory, one column of N*N words per lane
+//    after the staged parameters (element (i, j) of lane l at word
+//    (i*N + j)*32 + l, so a warp's access touches 32 consecutive words):
+//    held in registers next to u, F and the step it pushed the FP64 n = 8
+//    kernel into local memory.  The FP32 H of mixed mode fits in registers.
 //
 // Precision: as in the Newton kernels, the residual, its norm test and the
 // update of u are FP64; the Jacobian, jets, LU and B^-1 are FP64 or FP32
@@ -151,11 +156,26 @@ struct ThreadSolverBroyden : ThreadSolverBase<N, FAM, MIXED> {
     using Bs::nfev;
     using Bs::status;
 
-    P H[N][N]; // B^-1
+    static constexpr bool H_SMEM = !MIXED;
+    // shared memory per CTA: the staged parameters, then (FP64) H
+    static constexpr int H_OFFSET = (thread_smem_bytes<N, FAM, MIXED>() + 15) / 16 * 16;
+    static constexpr int SMEM = H_SMEM ? H_OFFSET + N * N * THREAD_TPB * (int)sizeof(P)
+                                       : thread_smem_bytes<N, FAM, MIXED>();
+
+    P *h;                          // FP64: this lane's B^-1, (i, j) at h[(i * N + j) * THREAD_TPB]
+    P hr[H_SMEM ? 1 : N * N];      // FP32: B^-1 in registers
     bool singular_next;
+
+    NLS_DI P &H(int i, int j)
+    {
+        if constexpr (H_SMEM) return h[(i * N + j) * THREAD_TPB];
+        else return hr[i * N + j];
+    }
 
     NLS_DI void init(const ParamView &pv, const SolveArgs &a, int64_t k)
     {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        h = reinterpret_cast<P *>(smem_raw + H_OFFSET) + threadIdx.x;
         Bs::init(pv, a, k);
         singular_next = false;
     }
@@ -184,13 +204,13 @@ struct ThreadSolverBroyden : ThreadSolverBase<N, FAM, MIXED> {
                     for (int i = 0; i < N; ++i) e[i] = (i == j) ? P(1) : P(0);
                     lu_apply<N, P>(J, piv, r, e);
 #pragma unroll
-                    for (int i = 0; i < N; ++i) H[i][j] = e[i];
+                    for (int i = 0; i < N; ++i) H(i, j) = e[i];
                 }
             } else {
 #pragma unroll
                 for (int i = 0; i < N; ++i)
 #pragma unroll
-                    for (int j = 0; j < N; ++j) H[i][j] = (i == j) ? P(1) : P(0);
+                    for (int j = 0; j < N; ++j) H(i, j) = (i == j) ? P(1) : P(0);
             }
         }
         // du = -H F, full step
@@ -201,7 +221,7 @@ struct ThreadSolverBroyden : ThreadSolverBase<N, FAM, MIXED> {
         for (int i = 0; i < N; ++i) {
             P s = P(0);
 #pragma unroll
-            for (int j = 0; j < N; ++j) s = fma(H[i][j], Fp[j], s);
+            for (int j = 0; j < N; ++j) s = fma(H(i, j), Fp[j], s);
             d[i] = -s;
         }
         double Fn[N];
@@ -219,8 +239,8 @@ struct ThreadSolverBroyden : ThreadSolverBase<N, FAM, MIXED> {
             P s = P(0), t = P(0);
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                s = fma(H[i][j], df[j], s);
-                t = fma(d[j], H[j][i], t);
+                s = fma(H(i, j), df[j], s);
+                t = fma(d[j], H(j, i), t);
             }
             Hdf[i] = s;
             w[i] = t; // (du^T H)_i
@@ -237,7 +257,7 @@ struct ThreadSolverBroyden : ThreadSolverBase<N, FAM, MIXED> {
                 for (int i = 0; i < N; ++i) {
                     const P c = (d[i] - Hdf[i]) * rd;
 #pragma unroll
-                    for (int j = 0; j < N; ++j) H[i][j] = fma(c, w[j], H[i][j]);
+                    for (int j = 0; j < N; ++j) H(i, j) = fma(c, w[j], H(i, j));
                 }
             } else {
                 singular_next = true;
@@ -258,6 +278,22 @@ struct ext_solver<N, FAM, MIXED, ALG_BROYDEN> {
     using type = ThreadSolverBroyden<N, FAM, MIXED>;
 };
 
+template <class S>
+struct ext_smem {
+    template <class T>
+    static constexpr int get(decltype(T::SMEM) *) { return T::SMEM; }
+    template <class T>
+    static constexpr int get(...) { return -1; }
+};
+
+template <int N, int FAM, bool MIXED, int ALG>
+constexpr int thread_ext_smem_bytes()
+{
+    using S = typename ext_solver<N, FAM, MIXED, ALG>::type;
+    constexpr int extra = ext_smem<S>::template get<S>(nullptr);
+    return extra >= 0 ? extra : thread_smem_bytes<N, FAM, MIXED>();
+}
+
 template <int N, int FAM, bool MIXED, int ALG>
 __global__ void __launch_bounds__(THREAD_TPB) k_solve_thread_ext(SolveArgs a)
 {
@@ -267,7 +303,7 @@ __global__ void __launch_bounds__(THREAD_TPB) k_solve_thread_ext(SolveArgs a)
 template <int N, int FAM, bool MIXED, int ALG>
 cudaError_t launch_thread_ext(const SolveArgs &a, int grid, cudaStream_t st)
 {
-    k_solve_thread_ext<N, FAM, MIXED, ALG><<<grid, THREAD_TPB, thread_smem_bytes<N, FAM, MIXED>(), st>>>(a);
+    k_solve_thread_ext<N, FAM, MIXED, ALG><<<grid, THREAD_TPB, thread_ext_smem_bytes<N, FAM, MIXED, ALG>(), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -278,7 +314,7 @@ KernelInfo thread_ext_info()
     k.launch = &launch_thread_ext<N, FAM, MIXED, ALG>;
     k.func = reinterpret_cast<const void *>(&k_solve_thread_ext<N, FAM, MIXED, ALG>);
     k.block = THREAD_TPB;
-    k.smem = thread_smem_bytes<N, FAM, MIXED>();
+    k.smem = thread_ext_smem_bytes<N, FAM, MIXED, ALG>();
     k.per_cta = THREAD_TPB;
     return k;
 }
