@@ -7,7 +7,7 @@ passage of the paper each step follows.
 """
 from .oracle import (  # noqa: F401
     ALG_NEWTON, ALG_NEWTON_BACKTRACK, ALG_TRUST_DOGLEG,
-    ALG_POTRA_PTAK, ALG_HALLEY, ALG_BROYDEN, ALG_MOD_BROYDEN,
+    ALG_POTRA_PTAK, ALG_HALLEY, ALG_BROYDEN, ALG_MOD_BROYDEN, ALG_TRUST_DOGLEG_NW,
     ST_SUCCESS, ST_MAXITERS, ST_SINGULAR, ST_NONFINITE, ST_LS_FAILED, ST_TR_STALLED,
     build, residual, jacobian, lu_factor, lu_solve, dogleg, solve_one, solve_trace,
     solve_batch, polish, polish_batch, adjoint, hvv, broyden_update,

@@ -24,6 +24,9 @@
  *                        du = (a o a) / (a + b/2) elementwise
  *   Sec. 2.1, Eq. 4      Potra-Ptak: two solves with the same J_k,
  *                        y = u + du1, u_{k+1} = y + du2 with J_k du2 = -f(y)
+ *   Sec. 2.2.2, Tab. 3   the NocedalWright radius update: Algorithm 4.1 of
+ *                        Nocedal & Wright, Numerical Optimization (the
+ *                        paper's reference for it)
  *   Sec. 3.1, Tab. 1     Broyden (identity start) and modified Broyden
  *                        (true Jacobian start), "good Broyden" update
  *
@@ -36,6 +39,9 @@
  *   an exactly zero or non-finite pivot is SINGULAR; the iteration count k
  *   counts loop passes (Jacobian uses, including rejected trust-region
  *   passes); Bratu's 1/h^2 is the exact integer (n+1)^2.
+ *   NocedalWright: eta = 1e-4, Delta_0 = 1, Delta_max = 1e3, 32 rejections
+ *   in a row -> TR_STALLED; "the step reaches the boundary" is the dogleg's
+ *   branch C or D.
  *   Halley: where a_i + b_i/2 is exactly zero the component of the step is
  *   a_i (the Newton component).  Potra-Ptak: both substeps are taken in
  *   every pass, the convergence test is on f(u_{k+1}).  Broyden: full steps,
@@ -50,7 +56,7 @@
 
 enum { FAM_CUBIC = 0, FAM_BRATU = 1, FAM_SQUARE = 2, FAM_ROSENBROCK = 3 };
 enum { ALG_NEWTON = 0, ALG_NEWTON_BACKTRACK = 1, ALG_TRUST_DOGLEG = 2, ALG_POTRA_PTAK = 4,
-       ALG_HALLEY = 5, ALG_BROYDEN = 6, ALG_MOD_BROYDEN = 7 };
+       ALG_HALLEY = 5, ALG_BROYDEN = 6, ALG_MOD_BROYDEN = 7, ALG_TRUST_DOGLEG_NW = 8 };
 enum { ST_SUCCESS = 0, ST_MAXITERS = 1, ST_SINGULAR = 2, ST_NONFINITE = 3,
        ST_LS_FAILED = 4, ST_TR_STALLED = 5 };
 
@@ -65,6 +71,8 @@ static const double TR_GROW = 2.0;
 static const double TR_SHRINK = 0.25;
 static const double TR_DELTA_MAX = 1e3;
 static const int TR_MAX_REJECTIONS = 32;
+/* Trust region, NocedalWright radius update (Nocedal & Wright, Alg. 4.1). */
+static const double TR_NW_ETA = 1e-4;
 
 int oracle_n_params(int family, int n)
 {
@@ -509,7 +517,31 @@ static void solve_one(int family, int n, const double *p, double *u, int alg, do
             pred = fF - dot(n, Jd, Jd);
             rho = (pred > 0.0 && all_finite(n, Ft)) ? ared / pred : -INFINITY;
             if (tr) { tr->branch[k - 1] = branch; tr->rho[k - 1] = rho; tr->radius[k - 1] = Delta; }
-            if (rho > 0.0) {
+            if (alg == ALG_TRUST_DOGLEG_NW) {
+                /* Nocedal & Wright, Algorithm 4.1: shrink when rho < 1/4,
+                 * grow when rho > 3/4 and the step reached the boundary,
+                 * accept when rho > eta (independently of the radius) */
+                int accept = rho > TR_NW_ETA;
+                if (rho < 0.25) {
+                    Delta = 0.25 * Delta;
+                } else if (rho > 0.75 && branch != 0) {
+                    Delta = 2.0 * Delta;
+                    if (Delta > TR_DELTA_MAX) Delta = TR_DELTA_MAX;
+                }
+                if (accept) {
+                    memcpy(u, ut, sizeof(double) * (size_t)n);
+                    memcpy(F, Ft, sizeof(double) * (size_t)n);
+                    need_jac = 1;
+                    rejections = 0;
+                } else {
+                    need_jac = 0;
+                    rejections++;
+                    if (rejections >= TR_MAX_REJECTIONS) {
+                        status = ST_TR_STALLED;
+                        goto done;
+                    }
+                }
+            } else if (rho > 0.0) {
                 memcpy(u, ut, sizeof(double) * (size_t)n);
                 memcpy(F, Ft, sizeof(double) * (size_t)n);
                 need_jac = 1;

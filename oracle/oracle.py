@@ -19,6 +19,7 @@ import numpy as np
 
 ALG_NEWTON, ALG_NEWTON_BACKTRACK, ALG_TRUST_DOGLEG = 0, 1, 2
 ALG_POTRA_PTAK, ALG_HALLEY, ALG_BROYDEN, ALG_MOD_BROYDEN = 4, 5, 6, 7
+ALG_TRUST_DOGLEG_NW = 8  # trust region with the NocedalWright radius update
 ST_SUCCESS, ST_MAXITERS, ST_SINGULAR, ST_NONFINITE, ST_LS_FAILED, ST_TR_STALLED = range(6)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
