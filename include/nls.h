@@ -83,7 +83,16 @@ enum nls_flags {
     NLS_ANALYTIC_JAC = 1 << 9, /* family's closed-form Jacobian instead of duals */
     NLS_TILE_THREAD = 1 << 10, /* force one instance per thread   (n <= 8)      */
     NLS_TILE_WARP = 1 << 11,   /* force one instance per warp     (n <= 32)     */
-    NLS_TILE_CTA = 1 << 12     /* force one instance per CTA      (n <= 128)    */
+    NLS_TILE_CTA = 1 << 12,    /* force one instance per CTA      (n <= 128)    */
+    NLS_TR_NOCEDAL_WRIGHT = 1 << 13 /* trust-region radius update of Tab. 3's
+                                  NocedalWright scheme (Nocedal & Wright,
+                                  Algorithm 4.1): shrink x1/4 iff rho < 1/4,
+                                  double (cap 1e3) iff rho > 3/4 and the step
+                                  reached the boundary, accept iff
+                                  rho > 1e-4.  Without it: accept iff rho > 0,
+                                  double iff rho > 3/4, shrink x1/4 on
+                                  rejection.  Valid with NLS_TRUST_DOGLEG and
+                                  NLS_POLYALG (its trust-region stage).      */
 };
 
 /* Per-instance outcome. */

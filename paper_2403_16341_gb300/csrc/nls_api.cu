@@ -600,8 +600,11 @@ static int validate(nls_batch *h, int family, const double *params, const double
     if (!(abstol >= 0.0) || !std::isfinite(abstol)) return fail(h, NLS_E_INVALID, "abstol must be finite and >= 0");
     const int a = alg & NLS_ALG_MASK;
     if (a > NLS_MOD_BROYDEN) return fail(h, NLS_E_INVALID, "unknown algorithm %d", a);
-    if (alg & ~(NLS_ALG_MASK | NLS_MIXED | NLS_ANALYTIC_JAC | NLS_TILE_THREAD | NLS_TILE_WARP | NLS_TILE_CTA))
+    if (alg & ~(NLS_ALG_MASK | NLS_MIXED | NLS_ANALYTIC_JAC | NLS_TILE_THREAD | NLS_TILE_WARP | NLS_TILE_CTA |
+                NLS_TR_NOCEDAL_WRIGHT))
         return fail(h, NLS_E_INVALID, "unknown flags in alg 0x%x", alg);
+    if ((alg & NLS_TR_NOCEDAL_WRIGHT) && a != NLS_TRUST_DOGLEG && a != NLS_POLYALG)
+        return fail(h, NLS_E_INVALID, "NLS_TR_NOCEDAL_WRIGHT needs a trust-region algorithm (alg %d)", a);
     if (batch > 0 && !u) return fail(h, NLS_E_INVALID, "u is NULL");
     if (batch > 0 && n_params(family, n) > 0 && !params) return fail(h, NLS_E_INVALID, "params is NULL");
     return NLS_OK;
@@ -717,6 +720,7 @@ int nls_solve(nls_handle h, int family, const double *params, double *u, int n, 
     r.args.ld = batch;
     r.args.n = n;
     r.args.alg = alg & NLS_ALG_MASK;
+    r.args.tr_scheme = (alg & NLS_TR_NOCEDAL_WRIGHT) ? nls::TR_NOCEDAL_WRIGHT : nls::TR_SIMPLE;
     r.args.abstol = abstol;
     r.args.maxiters = maxiters;
     r.args.budget_ns = (unsigned long long)h->opt.deadline_us * 1000ull;
@@ -909,6 +913,7 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
     base.ld = batch;
     base.n = n;
     base.alg = alg & NLS_ALG_MASK;
+    base.tr_scheme = (alg & NLS_TR_NOCEDAL_WRIGHT) ? nls::TR_NOCEDAL_WRIGHT : nls::TR_SIMPLE;
     base.abstol = abstol;
     base.maxiters = maxiters;
     Tuned best;

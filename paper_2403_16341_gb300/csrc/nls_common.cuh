@@ -41,6 +41,10 @@ constexpr double TR_GROW = 2.0;
 constexpr double TR_SHRINK = 0.25;
 constexpr double TR_DELTA_MAX = 1e3;
 constexpr int TR_MAX_REJECTIONS = 32;
+// NocedalWright radius update (Nocedal & Wright, Numerical Optimization,
+// Algorithm 4.1; Tab. 3): acceptance threshold eta
+constexpr double TR_NW_ETA = 1e-4;
+enum : int { TR_SIMPLE = 0, TR_NOCEDAL_WRIGHT = 1 };
 
 // Everything one launch needs for one uniform-size group of instances.
 struct SolveArgs {
@@ -65,7 +69,34 @@ struct SolveArgs {
     // > 0: stop iterating once this many nanoseconds of %globaltimer have
     // passed since the kernel started; unfinished instances end NLS_ABORTED
     unsigned long long budget_ns;
+    int tr_scheme; // TR_SIMPLE or TR_NOCEDAL_WRIGHT
 };
+
+// Outcome of one trust-region trial step (Sec. 2.2.2, Eq. 14): returns
+// whether the step is accepted and updates the radius.  ok: pred > 0 and
+// F(u + d) finite (otherwise rho = -inf); boundary: the dogleg step ended on
+// the region's boundary (branch C or D).  With pred > 0 every comparison of
+// rho = ared / pred with a threshold is ared against threshold * pred, so no
+// FP64 divide is taken.
+//   Simple: accept iff rho > 0; then double (capped) iff rho > 3/4;
+//           on rejection shrink to Delta / 4.
+//   NocedalWright: shrink to Delta / 4 iff rho < 1/4; else double (capped)
+//           iff rho > 3/4 and the step reached the boundary; accept iff
+//           rho > eta, independently of the radius change.
+NLS_DI bool tr_step_outcome(int scheme, bool ok, double ared, double pred, bool boundary, double &Delta)
+{
+    if (scheme == TR_NOCEDAL_WRIGHT) {
+        if (!ok || ared < 0.25 * pred) Delta *= TR_SHRINK;
+        else if (boundary && ared > TR_ETA_EXPAND * pred) Delta = fmin(TR_GROW * Delta, TR_DELTA_MAX);
+        return ok && ared > TR_NW_ETA * pred;
+    }
+    if (ok && ared > 0.0) {
+        if (ared > TR_ETA_EXPAND * pred) Delta = fmin(TR_GROW * Delta, TR_DELTA_MAX);
+        return true;
+    }
+    Delta *= TR_SHRINK;
+    return false;
+}
 
 NLS_DI unsigned long long global_ns()
 {

@@ -505,7 +505,7 @@ struct CtaSolver {
             const P JdJd = bsum(Jd * Jd, sm);
             const double pred = double(P(-2) * FJd - JdJd);
             const double ared = fF - fFt;
-            if (pred > 0.0 && mx < INF64_BITS && ared > 0.0) {
+            if (tr_step_outcome(A.tr_scheme, pred > 0.0 && mx < INF64_BITS, ared, pred, !(nN2 <= D2), Delta)) {
                 if (own) {
                     sm.u[t] = sm.ut[t];
                     sm.F[t] = f;
@@ -513,11 +513,9 @@ struct CtaSolver {
                 fF = fFt;
                 need_jac = true;
                 rej = 0;
-                if (ared > TR_ETA_EXPAND * pred) Delta = fmin(TR_GROW * Delta, TR_DELTA_MAX);
                 __syncthreads();
                 set_status_from(mx, A);
             } else {
-                Delta *= TR_SHRINK;
                 if (++rej >= TR_MAX_REJECTIONS) {
                     status = ST_TR_STALLED;
                     return;

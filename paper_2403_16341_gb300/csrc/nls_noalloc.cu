@@ -73,7 +73,9 @@ extern "C" int nls_solve_noalloc(void *cuda_stream, const nls_group *groups, int
     if (!(abstol >= 0.0) || !std::isfinite(abstol)) return err(NLS_E_INVALID, "abstol must be finite and >= 0");
     if (maxiters < 0) return err(NLS_E_INVALID, "negative maxiters");
     if ((alg & NLS_ALG_MASK) > NLS_TRUST_DOGLEG) return err(NLS_E_INVALID, "unknown algorithm %d", alg & NLS_ALG_MASK);
-    if (alg & ~(NLS_ALG_MASK | NLS_MIXED | NLS_ANALYTIC_JAC | NLS_TILE_THREAD))
+    if ((alg & NLS_TR_NOCEDAL_WRIGHT) && (alg & NLS_ALG_MASK) != NLS_TRUST_DOGLEG)
+        return err(NLS_E_INVALID, "NLS_TR_NOCEDAL_WRIGHT needs NLS_TRUST_DOGLEG");
+    if (alg & ~(NLS_ALG_MASK | NLS_MIXED | NLS_ANALYTIC_JAC | NLS_TILE_THREAD | NLS_TR_NOCEDAL_WRIGHT))
         return err(NLS_E_UNSUPPORTED, "nls_solve_noalloc runs the thread tiling only (flags 0x%x)", alg);
     nls::KernelInfo kern[NLS_NOALLOC_MAX_GROUPS];
     for (int g = 0; g < ngroups; ++g) {
@@ -107,6 +109,7 @@ extern "C" int nls_solve_noalloc(void *cuda_stream, const nls_group *groups, int
         a.ld = q.batch;
         a.n = q.n;
         a.alg = alg & NLS_ALG_MASK;
+        a.tr_scheme = (alg & NLS_TR_NOCEDAL_WRIGHT) ? nls::TR_NOCEDAL_WRIGHT : nls::TR_SIMPLE;
         a.abstol = abstol;
         a.maxiters = maxiters;
         a.status = q.out.status;

@@ -338,6 +338,7 @@ struct ThreadSolver {
             P nN2 = P(0);
 #pragma unroll
             for (int i = 0; i < N; ++i) nN2 = fma(dNp[i], dNp[i], nN2);
+            const bool boundary = !(nN2 <= D2);
             if (nN2 <= D2) {
 #pragma unroll
                 for (int i = 0; i < N; ++i) { d[i] = dN[i]; Jd[i] = -Fp[i]; }
@@ -387,16 +388,14 @@ struct ThreadSolver {
             for (int i = 0; i < N; ++i) { FJd = fma(Fp[i], Jd[i], FJd); JdJd = fma(Jd[i], Jd[i], JdJd); }
             const double pred = double(P(-2) * FJd - JdJd);
             const double ared = fF - fFt;
-            // pred > 0: rho > 0 <=> ared > 0, rho > eta <=> ared > eta pred (no FP64 divide)
-            if (pred > 0.0 && max_mag_bits(Ft) < INF64_BITS && ared > 0.0) {
+            const bool ok = pred > 0.0 && max_mag_bits(Ft) < INF64_BITS;
+            if (tr_step_outcome(a.tr_scheme, ok, ared, pred, boundary, Delta)) {
 #pragma unroll
                 for (int i = 0; i < N; ++i) { u[i] = ut[i]; F[i] = Ft[i]; }
                 fF = fFt;
                 need_jac = true;
                 rej = 0;
-                if (ared > TR_ETA_EXPAND * pred) Delta = fmin(TR_GROW * Delta, TR_DELTA_MAX);
             } else {
-                Delta *= TR_SHRINK;
                 if (++rej >= TR_MAX_REJECTIONS) {
                     status = ST_TR_STALLED;
                     return;

@@ -426,15 +426,13 @@ struct WarpSolver {
             const double ared = fF - fFt;
             if (go) {
                 ++nfev;
-                if (pred > 0.0 && fin && ared > 0.0) {
+                if (tr_step_outcome(A.tr_scheme, pred > 0.0 && fin, ared, pred, !(nN2 <= D2), Delta)) {
                     u = ut;
                     F = Ft;
                     fF = fFt;
                     need_jac = true;
                     rej = 0;
-                    if (ared > TR_ETA_EXPAND * pred) Delta = fmin(TR_GROW * Delta, TR_DELTA_MAX);
                 } else {
-                    Delta *= TR_SHRINK;
                     if (++rej >= TR_MAX_REJECTIONS) {
                         status = ST_TR_STALLED;
                         failed = true;

@@ -24,8 +24,9 @@ def gpu_solve(solver, batch, alg, abstol=1e-10, maxiters=50):
 
 
 def oracle_solve(batch, alg, abstol=1e-10, maxiters=50, threads=8):
+    oalg = O.ALG_TRUST_DOGLEG_NW if alg & (1 << 13) else ORACLE_ALG[alg & 0xFF]
     u, st, it, rs, nf = O.solve_batch(batch.family, batch.params, batch.u0,
-                                      ORACLE_ALG[alg & 0xFF], abstol, maxiters, threads=threads)
+                                      oalg, abstol, maxiters, threads=threads)
     return {"u": u, "status": st, "iters": it, "resid": rs, "nfev": nf}
 
 
