@@ -659,6 +659,40 @@ def run_workload(args, local):
                 res[f"{name}_{prec}"] = {"ms": ms, "solved": sv, "solved_per_s": sv / (ms / 1e3),
                                          "mean_iters": float(it.mean().item()),
                                          "launches": nl}
+    elif args.workload == "tr-schemes":
+        # trust-region radius updates: the Simple reading and NocedalWright
+        # (Tab. 3), on the cubic n = 8 workload and on Rosenbrock n = 8 from
+        # the Sec. 3.3 starts
+        nw = 1 << 13
+        cases = (("cubic8", I.workload_cubic_n8(args.instances), MAXITERS),
+                 ("rosenbrock8", I.rosenbrock_batch(8, 1 << 18, seed=0), 300))
+        line["config"] = (f"trust-region dogleg, Simple vs NocedalWright radius update: "
+                          f"{cases[0][1].batch} cubic n=8 (b ~ U[-5,5]^8, u0 = 0) and 2^18 "
+                          "generalized Rosenbrock n=8 (u0 ~ U[0,1)^8, maxiters 300)")
+        for cname, b, mi in cases:
+            dbs = _device_batches(torch, [b], dev)
+            _, p, u0, u, outs = dbs[0]
+            for sname, flag in (("simple", 0), ("nocedal_wright", nw)):
+                for prec, m in (("fp64", 0), ("mixed", MIXED)):
+                    alg = TR | flag | m
+                    times, solved = [], 0
+                    for r in range(max(args.warmup, 3) + args.steps):
+                        u.copy_(u0)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        q = solver.submit(b.family, p, u, alg, ABSTOL, mi, outs)
+                        solver.flush()
+                        e1.record(stream)
+                        sv = solver.wait(q)
+                        torch.cuda.synchronize()
+                        if r >= max(args.warmup, 3):
+                            times.append(e0.elapsed_time(e1))
+                            solved = sv
+                    ms = float(np.median(times))
+                    res[f"{cname}_{sname}_{prec}"] = {
+                        "ms": ms, "solved": solved, "solved_per_s": solved / (ms / 1e3),
+                        "mean_iters": float(outs[1][:b.batch].float().mean().item())}
     elif args.workload == "bratu-large":
         batches = I.workload_bratu_large()
         dbs = _device_batches(torch, batches, dev)
@@ -696,7 +730,7 @@ def main():
                     help="one-block-per-chunk grids instead of persistent ones (comparison runs)")
     ap.add_argument("--workload", default="cubic8",
                     choices=["cubic8", "cubic3", "uneven", "bratu-large", "serving", "adjoint",
-                             "poly", "next4"],
+                             "poly", "next4", "tr-schemes"],
                     help="cubic8: the benchmark step; the others print their own JSON line")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-Newton bar, the end-to-end leg and the CPU baseline")

@@ -375,8 +375,8 @@ struct CtaSolver {
             jacobian_tile(a, sm);
             if (tid < n) sm.Fp[tid] = P(sm.F[tid]);
             __syncthreads();
-            if (A.alg != ALG_NEWTON) {
-                // g = J^T F
+            if (A.alg == ALG_TRUST_DOGLEG) {
+                // g = J^T F and J g
 #pragma unroll
                 for (int bb = 0; bb < R; ++bb) {
                     P s = P(0);
@@ -393,22 +393,20 @@ struct CtaSolver {
                     sm.g[tid] = s;
                 }
                 __syncthreads();
-                if (A.alg == ALG_TRUST_DOGLEG) {
 #pragma unroll
-                    for (int aa = 0; aa < R; ++aa) {
-                        P s = P(0);
+                for (int aa = 0; aa < R; ++aa) {
+                    P s = P(0);
 #pragma unroll
-                        for (int bb = 0; bb < R; ++bb)
-                            if (col(bb) < n) s = fma(a[aa][bb], sm.g[col(bb)], s);
-                        sm.red[tx][row(aa)] = s;
-                    }
-                    __syncthreads();
-                    if (tid < n) {
-                        P s = P(0);
+                    for (int bb = 0; bb < R; ++bb)
+                        if (col(bb) < n) s = fma(a[aa][bb], sm.g[col(bb)], s);
+                    sm.red[tx][row(aa)] = s;
+                }
+                __syncthreads();
+                if (tid < n) {
+                    P s = P(0);
 #pragma unroll
-                        for (int q = 0; q < CTA_T; ++q) s += sm.red[q][tid];
-                        sm.Jg[tid] = s;
-                    }
+                    for (int q = 0; q < CTA_T; ++q) s += sm.red[q][tid];
+                    sm.Jg[tid] = s;
                 }
             }
             if (tid < n) sm.rhs[tid] = -sm.Fp[tid];
@@ -434,7 +432,8 @@ struct CtaSolver {
             need_jac = true;
             set_status_from(bmax(mag_bits(f), sm), A);
         } else if (A.alg == ALG_NEWTON_BACKTRACK) {
-            const P s = bsum(own ? sm.g[t] * P(sm.dN[t]) : P(0), sm);
+            // slope F^T J dN of Eq. 9 by linearity: J dN = -F, so it is -||F||^2
+            const double s = -fF;
             const double phi0 = 0.5 * fF;
             double alpha = 1.0;
             bool ok = false;
@@ -446,7 +445,7 @@ struct CtaSolver {
                 ++nfev;
                 fFt = bsum(f * f, sm);
                 const uint64_t mx = bmax(mag_bits(f), sm);
-                if (mx < INF64_BITS && 0.5 * fFt <= phi0 + LS_C1 * alpha * double(s)) {
+                if (mx < INF64_BITS && 0.5 * fFt <= phi0 + LS_C1 * alpha * s) {
                     ok = true;
                     if (own) {
                         sm.u[t] = sm.ut[t];

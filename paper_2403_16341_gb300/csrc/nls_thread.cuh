@@ -276,9 +276,8 @@ struct ThreadSolver {
             jacobian(pv, u, J);
 #pragma unroll
             for (int i = 0; i < N; ++i) Fp[i] = P(F[i]);
-            // g = J^T F (gradient of 1/2 ||F||^2), taken before J is factored; the
-            // trust region forms g and J g only when the Newton step leaves the region
-            if (a.alg == ALG_NEWTON_BACKTRACK) gradient(J, false);
+            // the trust region forms g = J^T F and J g only when the Newton step
+            // leaves the region (J is re-evaluated then: the LU overwrites it)
             have_g = false;
 #pragma unroll
             for (int i = 0; i < N; ++i) b[i] = -Fp[i];
@@ -301,10 +300,9 @@ struct ThreadSolver {
             ++nfev;
             need_jac = true;
         } else if (a.alg == ALG_NEWTON_BACKTRACK) {
-            // slope F^T J dN = g . dN (Eq. 9); phi(alpha) = 1/2 ||F(u + alpha dN)||^2
-            P s = P(0);
-#pragma unroll
-            for (int i = 0; i < N; ++i) s = fma(g[i], dNp[i], s);
+            // slope F^T J dN of Eq. 9 by linearity: J dN = -F, so it is -||F||^2
+            // (no J^T F is formed); phi(alpha) = 1/2 ||F(u + alpha dN)||^2
+            const double s = -fF;
             const double phi0 = 0.5 * fF;
             double alpha = 1.0;
             bool ok = false;
@@ -315,7 +313,7 @@ struct ThreadSolver {
                 residual(pv, ut, Ft);
                 ++nfev;
                 const double fFt = sumsq(Ft);
-                if (max_mag_bits(Ft) < INF64_BITS && 0.5 * fFt <= phi0 + LS_C1 * alpha * double(s)) {
+                if (max_mag_bits(Ft) < INF64_BITS && 0.5 * fFt <= phi0 + LS_C1 * alpha * s) {
 #pragma unroll
                     for (int i = 0; i < N; ++i) { u[i] = ut[i]; F[i] = Ft[i]; }
                     fF = fFt;

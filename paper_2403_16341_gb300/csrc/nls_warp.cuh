@@ -310,8 +310,8 @@ struct WarpSolver {
             jacobian_row(a);
             const P fp = P(F);
             if (fresh) Fp = fp;
-            if (A.alg != ALG_NEWTON) {
-                // g = J^T F: column sums of F_r * row r
+            if (A.alg == ALG_TRUST_DOGLEG) {
+                // g = J^T F: column sums of F_r * row r, and J g
 #pragma unroll
                 for (int j = 0; j < L; ++j) sm.tr[r][j] = a[j] * fp;
                 __syncwarp();
@@ -320,15 +320,13 @@ struct WarpSolver {
                 for (int i = 0; i < L; ++i) s += sm.tr[i][r];
                 __syncwarp();
                 if (fresh) g = s;
-                if (A.alg == ALG_TRUST_DOGLEG) {
-                    sm.vec[r] = s;
-                    __syncwarp();
-                    P t = P(0);
+                sm.vec[r] = s;
+                __syncwarp();
+                P t = P(0);
 #pragma unroll
-                    for (int j = 0; j < L; ++j) t = fma(a[j], sm.vec[j], t);
-                    __syncwarp();
-                    if (fresh) Jg = t;
-                }
+                for (int j = 0; j < L; ++j) t = fma(a[j], sm.vec[j], t);
+                __syncwarp();
+                if (fresh) Jg = t;
             }
             P b = -fp;
             const bool ok = lu_solve(a, b, sm);
@@ -354,7 +352,8 @@ struct WarpSolver {
                 need_jac = true;
             }
         } else if (A.alg == ALG_NEWTON_BACKTRACK) {
-            const P s = seg_sum<L>(g * P(dN), 0xffffffffu);
+            // slope F^T J dN of Eq. 9 by linearity: J dN = -F, so it is -||F||^2
+            const double s = -fF;
             const double phi0 = 0.5 * fF;
             double alpha = 1.0;
             bool trying = go, ok = false;
@@ -366,7 +365,7 @@ struct WarpSolver {
                 const bool fin = seg_max<L>(mag_bits(Ft), 0xffffffffu) < INF64_BITS;
                 if (trying) {
                     ++nfev;
-                    if (fin && 0.5 * fFt <= phi0 + LS_C1 * alpha * double(s)) {
+                    if (fin && 0.5 * fFt <= phi0 + LS_C1 * alpha * s) {
                         u = ut;
                         F = Ft;
                         fF = fFt;
