@@ -56,15 +56,16 @@ def algorithmic_fp64_flops(n: int, alg: int, iters: np.ndarray, nfev: np.ndarray
     cubic: 2n^2 + 3n, plus 2n for the squared norm and 2n for forming the
     trial point.  In FP64 mode every pass also factors and solves:
     LU 2n^3/3 - n^2/2 - n/6, triangular solves 2n^2, analytic-equivalent
-    Jacobian 2n, J^T F 2n^2 (line search), 10n for the dogleg's scalar work
-    (trust region; J^T F and J g are formed only when the Newton step leaves
-    the region, so they are not counted).  Mixed mode runs the Jacobian and
-    the LU in FP32, so only the residual-side terms are FP64."""
+    Jacobian 2n, and 10n for the dogleg's scalar work (trust region).  The
+    line search's slope F^T J dN is -||F||^2 by linearity and the trust
+    region forms J^T F and J g only when the Newton step leaves the region,
+    so neither matrix-vector product is counted.  Mixed mode runs the
+    Jacobian and the LU in FP32, so only the residual-side terms are FP64."""
     res = (2 * n * n + 3 * n) + 2 * n + 2 * n
     f = float(nfev.sum()) * res
     if not alg & MIXED:
         per_pass = (2 * n ** 3 / 3 - n * n / 2 - n / 6) + 2 * n * n + 2 * n
-        per_pass += 2 * n * n if (alg & 0xFF) == LS else 10 * n
+        per_pass += 0 if (alg & 0xFF) == LS else 10 * n
         f += float(iters.sum()) * per_pass
     return f
 
