@@ -43,7 +43,7 @@ struct CtaSmem {
     int row_pos[CTA_NMAX];  // position of row i after the interchanges so far
     uint64_t ckey[2];       // pivot of step k in slot k & 1: key, position, row
     int cpos[2], crow[2];
-    double rd[CTA_TPB / 32];
+    double rd[3][CTA_TPB / 32];
     uint64_t rm[CTA_TPB / 32];
     long long inst;
     int late;
@@ -76,19 +76,59 @@ struct CtaSolver {
     NLS_DI int col(int b) const { return tx + CTA_T * b; }
 
     // ------------------------------------------------------------ reductions
-    NLS_DI double bsum(double v, SM &sm) const
+    // K block sums with one pair of barriers (warps summed in a fixed order,
+    // so every thread gets the same, reproducible value)
+    template <int K>
+    NLS_DI void bsumk(double (&v)[K], SM &sm) const
     {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sm.rd[warp] = v;
-        __syncthreads();
-        double s = 0.0;
+        for (int j = 0; j < K; ++j) {
 #pragma unroll
-        for (int w = 0; w < CTA_TPB / 32; ++w) s += sm.rd[w];
+            for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+            if (lane == 0) sm.rd[j][warp] = v[j];
+        }
         __syncthreads();
-        return s;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < CTA_TPB / 32; ++w) s += sm.rd[j][w];
+            v[j] = s;
+        }
+        __syncthreads();
+    }
+    NLS_DI double bsum(double v, SM &sm) const
+    {
+        double a[1] = {v};
+        bsumk<1>(a, sm);
+        return a[0];
     }
     NLS_DI float bsum(float v, SM &sm) const { return float(bsum(double(v), sm)); }
+    // block sum of v and block max of m with one pair of barriers
+    NLS_DI void bsum_max(double &v, uint64_t &m, SM &sm) const
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+            const uint64_t w = __shfl_xor_sync(0xffffffffu, m, o);
+            m = w > m ? w : m;
+        }
+        if (lane == 0) {
+            sm.rd[0][warp] = v;
+            sm.rm[warp] = m;
+        }
+        __syncthreads();
+        double s = 0.0;
+        uint64_t x = 0;
+#pragma unroll
+        for (int w = 0; w < CTA_TPB / 32; ++w) {
+            s += sm.rd[0][w];
+            x = sm.rm[w] > x ? sm.rm[w] : x;
+        }
+        __syncthreads();
+        v = s;
+        m = x;
+    }
     NLS_DI uint64_t bmax(uint64_t v, SM &sm) const
     {
 #pragma unroll
@@ -362,8 +402,10 @@ struct CtaSolver {
         Delta = TR_DELTA0;
         need_jac = true;
         status = ST_RUNNING;
-        fF = bsum(f * f, sm);
-        set_status_from(bmax(mag_bits(f), sm), A);
+        fF = f * f;
+        uint64_t mx = mag_bits(f);
+        bsum_max(fF, mx, sm);
+        set_status_from(mx, A);
         if (status == ST_RUNNING && A.maxiters <= 0) status = ST_MAXITERS;
     }
 
@@ -443,8 +485,9 @@ struct CtaSolver {
                 __syncthreads();
                 f = residual_t(sm.ut);
                 ++nfev;
-                fFt = bsum(f * f, sm);
-                const uint64_t mx = bmax(mag_bits(f), sm);
+                fFt = f * f;
+                uint64_t mx = mag_bits(f);
+                bsum_max(fFt, mx, sm);
                 if (mx < INF64_BITS && 0.5 * fFt <= phi0 + LS_C1 * alpha * s) {
                     ok = true;
                     if (own) {
@@ -465,44 +508,48 @@ struct CtaSolver {
             need_jac = true;
         } else {
             const double dn = own ? sm.dN[t] : 0.0;
-            const P gt = own ? sm.g[t] : P(0), jgt = own ? sm.Jg[t] : P(0), fpt = own ? sm.Fp[t] : P(0);
+            const P gt = own ? sm.g[t] : P(0), jgt = own ? sm.Jg[t] : P(0);
             const P D2 = P(Delta * Delta);
-            const P nN2 = bsum(P(dn) * P(dn), sm);
-            const P gg = bsum(gt * gt, sm);
-            const P JgJg = bsum(jgt * jgt, sm);
+            double r3[3] = {double(P(dn) * P(dn)), double(gt * gt), double(jgt * jgt)};
+            bsumk<3>(r3, sm);
+            const P nN2 = P(r3[0]), gg = P(r3[1]), JgJg = P(r3[2]);
             const P tt = gg / JgJg;
             const P cc = tt * tt * gg;
             const P w = P(dn) + tt * gt;
-            const P aa = bsum(w * w, sm);
-            const P bb = bsum(-tt * gt * w, sm);
-            double d;
-            P Jd;
+            // the interpolation's quadratic, only when the CTA takes branch D
+            // (a block-uniform decision, so the barriers inside are safe)
+            P aa = P(0), bb = P(0);
+            if (!(nN2 <= D2) && !(cc >= D2)) {
+                double r2[2] = {double(w * w), double(-tt * gt * w)};
+                bsumk<2>(r2, sm);
+                aa = P(r2[0]);
+                bb = P(r2[1]);
+            }
+            // pred = -2 F.Jd - ||Jd||^2 (Eq. 14) from block-uniform scalars:
+            // J dN = -F and F.(J g) = g.g (g = J^T F), so no J d is formed
+            double d, pred;
             if (nN2 <= D2) {
                 d = dn;
-                Jd = -fpt;
+                pred = fF;
             } else if (cc >= D2) {
                 const P sc = P(Delta) / nls_sqrt(gg);
                 d = double(-sc * gt);
-                Jd = -sc * jgt;
+                pred = double(sc * (P(2) * gg - sc * JgJg));
             } else {
                 const P q = cc - D2;
                 const P tau = (-bb + nls_sqrt(bb * bb - aa * q)) / aa;
                 d = double(fma(tau, w, -tt * gt));
-                Jd = -(P(1) - tau) * tt * jgt - tau * fpt;
+                const P s1 = (P(1) - tau) * tt; // J d = -s1 J g - tau F
+                pred = double(s1 * (P(2) * (P(1) - tau) * gg - s1 * JgJg) + tau * (P(2) - tau) * P(fF));
             }
-            if (!own) {
-                d = 0.0;
-                Jd = P(0);
-            }
+            if (!own) d = 0.0;
             if (own) sm.ut[t] = sm.u[t] + d;
             __syncthreads();
             const double f = residual_t(sm.ut);
             ++nfev;
-            const double fFt = bsum(f * f, sm);
-            const uint64_t mx = bmax(mag_bits(f), sm);
-            const P FJd = bsum(fpt * Jd, sm);
-            const P JdJd = bsum(Jd * Jd, sm);
-            const double pred = double(P(-2) * FJd - JdJd);
+            double fFt = f * f;
+            uint64_t mx = mag_bits(f);
+            bsum_max(fFt, mx, sm);
             const double ared = fF - fFt;
             if (tr_step_outcome(A.tr_scheme, pred > 0.0 && mx < INF64_BITS, ared, pred, !(nN2 <= D2), Delta)) {
                 if (own) {

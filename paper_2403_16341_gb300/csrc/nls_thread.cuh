@@ -329,9 +329,11 @@ struct ThreadSolver {
             need_jac = true;
         } else {
             // Powell's dogleg on m(d) = 1/2||F||^2 + d^T J^T F + 1/2 d^T J^T J d, ||d||_2 <= Delta.
-            // J d follows from linearity: J dN = -F, J c = -t J g (c = -t g).
+            // pred = ||F||^2 - ||F + J d||^2 = -2 F.Jd - ||Jd||^2 (Eq. 14) by linearity:
+            // J dN = -F and, with g = J^T F, F.(J g) = g.g, so every branch's pred is
+            // a combination of ||F||^2, ||g||^2 and ||J g||^2 (no vector J d is formed).
             double d[N];
-            P Jd[N];
+            double pred;
             const P D2 = P(Delta * Delta);
             P nN2 = P(0);
 #pragma unroll
@@ -339,7 +341,8 @@ struct ThreadSolver {
             const bool boundary = !(nN2 <= D2);
             if (nN2 <= D2) {
 #pragma unroll
-                for (int i = 0; i < N; ++i) { d[i] = dN[i]; Jd[i] = -Fp[i]; }
+                for (int i = 0; i < N; ++i) d[i] = dN[i];
+                pred = fF; // J dN = -F
             } else {
                 if (!have_g) {
                     // J at the same u again (the LU overwrote it): same values as before
@@ -356,7 +359,8 @@ struct ThreadSolver {
                 if (cc >= D2) {
                     const P sc = P(Delta) / nls_sqrt(gg);
 #pragma unroll
-                    for (int i = 0; i < N; ++i) { d[i] = double(-sc * g[i]); Jd[i] = -sc * Jg[i]; }
+                    for (int i = 0; i < N; ++i) d[i] = double(-sc * g[i]);
+                    pred = double(sc * (P(2) * gg - sc * JgJg)); // J d = -sc J g
                 } else {
                     P w[N], aa = P(0), bb = P(0);
 #pragma unroll
@@ -368,10 +372,10 @@ struct ThreadSolver {
                     const P q = cc - D2;
                     const P tau = (-bb + nls_sqrt(bb * bb - aa * q)) / aa;
 #pragma unroll
-                    for (int i = 0; i < N; ++i) {
-                        d[i] = double(fma(tau, w[i], -t * g[i]));
-                        Jd[i] = -(P(1) - tau) * t * Jg[i] - tau * Fp[i];
-                    }
+                    for (int i = 0; i < N; ++i) d[i] = double(fma(tau, w[i], -t * g[i]));
+                    // J d = -s1 J g - tau F with s1 = (1 - tau) t
+                    const P s1 = (P(1) - tau) * t;
+                    pred = double(s1 * (P(2) * (P(1) - tau) * gg - s1 * JgJg) + tau * (P(2) - tau) * P(fF));
                 }
             }
             double ut[N], Ft[N];
@@ -380,11 +384,7 @@ struct ThreadSolver {
             residual(pv, ut, Ft);
             ++nfev;
             const double fFt = sumsq(Ft);
-            // rho = ared / pred (Eq. 14); pred = ||F||^2 - ||F + J d||^2 = -2 F.Jd - ||Jd||^2
-            P FJd = P(0), JdJd = P(0);
-#pragma unroll
-            for (int i = 0; i < N; ++i) { FJd = fma(Fp[i], Jd[i], FJd); JdJd = fma(Jd[i], Jd[i], JdJd); }
-            const double pred = double(P(-2) * FJd - JdJd);
+            // rho = ared / pred (Eq. 14)
             const double ared = fF - fFt;
             const bool ok = pred > 0.0 && max_mag_bits(Ft) < INF64_BITS;
             if (tr_step_outcome(a.tr_scheme, ok, ared, pred, boundary, Delta)) {

@@ -396,32 +396,28 @@ struct WarpSolver {
             const P w = P(dN) + t * g; // dN - c
             const P aa = seg_sum<L>(w * w, 0xffffffffu);
             const P bb = seg_sum<L>(-t * g * w, 0xffffffffu);
-            double d;
-            P Jd;
+            // pred = -2 F.Jd - ||Jd||^2 (Eq. 14) from segment-uniform scalars:
+            // J dN = -F and F.(J g) = g.g (g = J^T F), so no J d is formed
+            double d, pred;
             if (nN2 <= D2) {
                 d = dN;
-                Jd = -Fp;
+                pred = fF;
             } else if (cc >= D2) {
                 const P sc = P(Delta) / nls_sqrt(gg);
                 d = double(-sc * g);
-                Jd = -sc * Jg;
+                pred = double(sc * (P(2) * gg - sc * JgJg));
             } else {
                 const P q = cc - D2;
                 const P tau = (-bb + nls_sqrt(bb * bb - aa * q)) / aa;
                 d = double(fma(tau, w, -t * g));
-                Jd = -(P(1) - tau) * t * Jg - tau * Fp;
+                const P s1 = (P(1) - tau) * t; // J d = -s1 J g - tau F
+                pred = double(s1 * (P(2) * (P(1) - tau) * gg - s1 * JgJg) + tau * (P(2) - tau) * P(fF));
             }
-            if (!row_live()) {
-                d = 0.0;
-                Jd = P(0);
-            }
+            if (!row_live()) d = 0.0;
             const double ut = u + d;
             const double Ft = residual(ut, sm, 0xffffffffu);
             const double fFt = seg_sum<L>(Ft * Ft, 0xffffffffu);
             const bool fin = seg_max<L>(mag_bits(Ft), 0xffffffffu) < INF64_BITS;
-            const P FJd = seg_sum<L>(Fp * Jd, 0xffffffffu);
-            const P JdJd = seg_sum<L>(Jd * Jd, 0xffffffffu);
-            const double pred = double(P(-2) * FJd - JdJd);
             const double ared = fF - fFt;
             if (go) {
                 ++nfev;
