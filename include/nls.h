@@ -164,10 +164,12 @@ int nls_solve(nls_handle h, int family, const double *params, double *u, int n, 
  * float64[n * batch]) this computes, per instance, mu from J^T mu = w and
  * grad = dL/dtheta = -mu^T dF/dtheta (DEVICE float64[E * batch], the family's
  * parameter layout).  status (DEVICE int32[batch], may be NULL) receives
- * NLS_SUCCESS or NLS_SINGULAR.  FP64, one instance per thread, n <= 8.
+ * NLS_SUCCESS or NLS_SINGULAR.  FP64, forward-mode Jacobian; one instance
+ * per thread (n <= 8), per warp segment (n <= 32) or per CTA (n <= 128).
  * Enqueued on the handle's stream at once (not grouped with nls_solve
  * requests); order it after the solve that produced u.
- * Errors: NLS_E_INVALID, NLS_E_UNSUPPORTED (n > 8, unknown family), NLS_E_CUDA. */
+ * Errors: NLS_E_INVALID, NLS_E_UNSUPPORTED (n > 128, unknown family),
+ * NLS_E_CUDA. */
 int nls_adjoint(nls_handle h, int family, const double *params, const double *u, int n,
                 int64_t batch, const double *w, double *grad, int32_t *status);
 

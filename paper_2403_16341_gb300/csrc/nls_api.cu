@@ -941,14 +941,15 @@ int nls_adjoint(nls_handle h, int family, const double *params, const double *u,
 {
     if (!h) return NLS_E_INVALID;
     if (family < 0 || family > FAM_ROSENBROCK) return fail(h, NLS_E_UNSUPPORTED, "unknown family %d", family);
-    if (n < 1 || n > 8) return fail(h, NLS_E_UNSUPPORTED, "nls_adjoint holds n <= 8 (n = %d)", n);
+    if (n < 1 || n > 128) return fail(h, NLS_E_UNSUPPORTED, "nls_adjoint holds n <= 128 (n = %d)", n);
     if (batch < 0) return fail(h, NLS_E_INVALID, "negative batch");
     if (batch == 0) return NLS_OK;
     if (!u || !w) return fail(h, NLS_E_INVALID, "u or w is NULL");
     if (n_params(family, n) > 0 && (!params || !grad)) return fail(h, NLS_E_INVALID, "params or grad is NULL");
     if ((batch + 31) / 32 > INT32_MAX) return fail(h, NLS_E_INVALID, "batch too large");
     NLS_CUDA(h, cudaSetDevice(h->device));
-    cudaError_t e = nls::launch_adjoint(family, n, params, u, w, grad, status, batch, h->stream);
+    cudaError_t e = n <= 8 ? nls::launch_adjoint(family, n, params, u, w, grad, status, batch, h->stream)
+                           : nls::launch_adjoint_tiles(family, n, params, u, w, grad, status, batch, h->stream);
     if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "adjoint launch: %s", cudaGetErrorString(e));
     ++h->launches;
     return NLS_OK;

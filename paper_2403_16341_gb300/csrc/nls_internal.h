@@ -38,9 +38,12 @@ KernelInfo cta_kernel(int family, int n, bool mixed);
 } // namespace nls
 
 namespace nls {
-// Adjoint sensitivity kernels (one instance per thread, n <= 8).
+// Adjoint sensitivity kernels: one instance per thread (n <= 8), ...
 cudaError_t launch_adjoint(int family, int n, const double *params, const double *u, const double *w,
                            double *grad, int32_t *status, int64_t batch, cudaStream_t st);
+// ... per warp segment (n <= 32) or per CTA (n <= 128).
+cudaError_t launch_adjoint_tiles(int family, int n, const double *params, const double *u, const double *w,
+                                 double *grad, int32_t *status, int64_t batch, cudaStream_t st);
 } // namespace nls
 
 namespace nls {
