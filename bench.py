@@ -584,31 +584,38 @@ def run_workload(args, local):
         for name, alg in (("mixed", LS | MIXED), ("fp64", LS), ("mixed_again", LS | MIXED)):
             res[name] = run_serving(args, nls, local, alg=alg)
     elif args.workload == "adjoint":
-        # sensitivities of 2^20 cubic n = 8 roots: dL/d(A, b) for cotangents w
-        b = I.workload_cubic_n8()
-        dbs = _device_batches(torch, [b], dev)
-        _, p, u0, u, outs = dbs[0]
-        u.copy_(u0)
-        solver.wait(solver.submit(b.family, p, u, LS | MIXED, ABSTOL, MAXITERS, outs))
-        w = torch.randn_like(u0)
-        grad = torch.empty_like(p)
-        st = torch.empty(b.batch, dtype=torch.int32, device=dev)
-        times = []
-        for r in range(max(args.warmup, 3) + args.steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            nls.nls_adjoint(solver.h, b.family, p.data_ptr(), u.data_ptr(), N_SYS, b.batch,
-                            w.data_ptr(), grad.data_ptr(), st.data_ptr())
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if r >= max(args.warmup, 3):
-                times.append(e0.elapsed_time(e1))
-        ms = float(np.median(times))
-        bytes_moved = b.batch * 8 * (b.params.shape[0] * 2 + 2 * N_SYS) + b.batch * 4
-        line["config"] = "adjoint sensitivities of 2^20 cubic n=8 roots (FP64, one instance per thread)"
-        res["adjoint"] = {"ms": ms, "instances_per_s": b.batch / (ms / 1e3),
-                          "hbm_gbs": bytes_moved / (ms / 1e3) / 1e9,
-                          "singular": int((st != 0).sum().item())}
+        # sensitivities dL/dtheta of solved roots for random cotangents w, one
+        # case per tiling: 2^20 cubic n = 8 (thread), 2^16 cubic n = 32 (warp
+        # segment), 8192 Bratu n = 128 (CTA)
+        cases = (("cubic8_thread", I.workload_cubic_n8()),
+                 ("cubic32_warp", I.cubic_batch(32, 1 << 16, config_id=2)),
+                 ("bratu128_cta", I.bratu_batch(128, 8192, config_id=2)))
+        line["config"] = ("adjoint sensitivities (FP64): 2^20 cubic n=8 roots (thread), 2^16 cubic "
+                          "n=32 (warp), 8192 Bratu n=128 (CTA)")
+        for name, b in cases:
+            dbs = _device_batches(torch, [b], dev)
+            _, p, u0, u, outs = dbs[0]
+            u.copy_(u0)
+            solver.wait(solver.submit(b.family, p, u, LS | MIXED, ABSTOL, MAXITERS, outs))
+            w = torch.randn_like(u0)
+            grad = torch.empty_like(p)
+            st = torch.empty(b.batch, dtype=torch.int32, device=dev)
+            times = []
+            for r in range(max(args.warmup, 3) + args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                nls.nls_adjoint(solver.h, b.family, p.data_ptr(), u.data_ptr(), b.n, b.batch,
+                                w.data_ptr(), grad.data_ptr(), st.data_ptr())
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if r >= max(args.warmup, 3):
+                    times.append(e0.elapsed_time(e1))
+            ms = float(np.median(times))
+            # params read, gradient written, root and cotangent read, status written
+            bytes_moved = b.batch * 8 * (b.params.shape[0] * 2 + 2 * b.n) + b.batch * 4
+            res[name] = {"ms": ms, "instances_per_s": b.batch / (ms / 1e3),
+                         "hbm_gbs": bytes_moved / (ms / 1e3) / 1e9,
+                         "singular": int((st != 0).sum().item())}
     elif args.workload == "poly":
         # Rosenbrock n = 8 from the Sec. 3.3 starts, every third moved to the
         # Fig. 1 start where plain Newton fails
