@@ -62,6 +62,26 @@ KernelInfo thread_ext_kernel(int family, int n, int alg, bool mixed)
     return table[row][family](n, mixed);
 }
 
+KernelInfo warp_potra_ptak_fp64(int family, int L);
+KernelInfo warp_potra_ptak_mixed(int family, int L);
+KernelInfo warp_halley_fp64(int family, int L);
+KernelInfo warp_halley_mixed(int family, int L);
+KernelInfo warp_broyden_fp64(int family, int L);
+KernelInfo warp_broyden_mixed(int family, int L);
+
+// Potra-Ptak, Halley, Broyden and modified Broyden, one instance per warp
+// segment of L = 16 or 32 lanes.
+KernelInfo warp_ext_kernel(int family, int L, int alg, bool mixed)
+{
+    switch (alg) {
+    case ALG_POTRA_PTAK: return mixed ? warp_potra_ptak_mixed(family, L) : warp_potra_ptak_fp64(family, L);
+    case ALG_HALLEY: return mixed ? warp_halley_mixed(family, L) : warp_halley_fp64(family, L);
+    case ALG_BROYDEN:
+    case ALG_MOD_BROYDEN: return mixed ? warp_broyden_mixed(family, L) : warp_broyden_fp64(family, L);
+    default: return KernelInfo{};
+    }
+}
+
 KernelInfo warp_kernel_fp64(int family, int L);
 KernelInfo warp_kernel_mixed(int family, int L);
 
@@ -239,14 +259,20 @@ static int select_kernel(nls_batch *h, int family, int n, int alg, KernelInfo *o
         }
     }
     if ((alg & NLS_ALG_MASK) >= NLS_POTRA_PTAK) {
-        if (tiles && tiles != NLS_TILE_THREAD)
-            return fail(h, NLS_E_UNSUPPORTED, "algorithm %d runs one instance per thread only", alg & NLS_ALG_MASK);
-        if (analytic)
-            return fail(h, NLS_E_UNSUPPORTED, "algorithm %d takes derivatives by forward mode only",
-                        alg & NLS_ALG_MASK);
-        if (n > 8) return fail(h, NLS_E_UNSUPPORTED, "algorithm %d holds n <= 8 (n = %d)", alg & NLS_ALG_MASK, n);
-        tiles = NLS_TILE_THREAD;
-        *out = nls::thread_ext_kernel(family, n, alg & NLS_ALG_MASK, mixed);
+        const int a = alg & NLS_ALG_MASK;
+        if (tiles == NLS_TILE_CTA)
+            return fail(h, NLS_E_UNSUPPORTED, "algorithm %d runs per thread or per warp segment only", a);
+        if (analytic) return fail(h, NLS_E_UNSUPPORTED, "algorithm %d takes derivatives by forward mode only", a);
+        if (n > 32) return fail(h, NLS_E_UNSUPPORTED, "algorithm %d holds n <= 32 (n = %d)", a, n);
+        if (!tiles) tiles = n <= 8 ? NLS_TILE_THREAD : NLS_TILE_WARP;
+        if (tiles == NLS_TILE_THREAD) {
+            if (n > 8) return fail(h, NLS_E_UNSUPPORTED, "thread tiling holds n <= 8 (n = %d)", n);
+            *out = nls::thread_ext_kernel(family, n, a, mixed);
+        } else {
+            int L = (lanes == 16 || lanes == 32) && lanes >= n ? lanes : (n <= 16 ? 16 : 32);
+            lanes = L;
+            *out = nls::warp_ext_kernel(family, L, a, mixed);
+        }
     } else {
         if (!tiles) tiles = n <= 8 ? NLS_TILE_THREAD : n <= 32 ? NLS_TILE_WARP : NLS_TILE_CTA;
     }
@@ -861,9 +887,8 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
         return fail(h, NLS_E_INVALID, "nls_autotune chooses the tiling: pass no tiling flag");
     if ((alg & NLS_ALG_MASK) == NLS_POLYALG)
         return fail(h, NLS_E_INVALID, "tune the stage algorithms, not NLS_POLYALG");
-    if ((alg & NLS_ALG_MASK) >= NLS_POTRA_PTAK && ((alg & NLS_ANALYTIC_JAC) || n > 8))
-        return fail(h, NLS_E_UNSUPPORTED, "algorithm %d: one instance per thread (n <= 8), forward-mode derivatives",
-                    alg & NLS_ALG_MASK);
+    if ((alg & NLS_ALG_MASK) >= NLS_POTRA_PTAK && ((alg & NLS_ANALYTIC_JAC) || n > 32))
+        return fail(h, NLS_E_UNSUPPORTED, "algorithm %d: n <= 32, forward-mode derivatives", alg & NLS_ALG_MASK);
     NLS_CUDA(h, cudaSetDevice(h->device));
     rc = flush_pending(h);
     if (rc) return rc;
@@ -896,7 +921,12 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
     };
     const bool ext = (alg & NLS_ALG_MASK) >= NLS_POTRA_PTAK;
     if (ext) {
-        for (int r : {REFILL_STATIC, 0, 16, 24, 31}) add(NLS_TILE_THREAD, 0, r);
+        if (n <= 8)
+            for (int r : {REFILL_STATIC, 0, 16, 24, 31}) add(NLS_TILE_THREAD, 0, r);
+        for (int r : {REFILL_STATIC, -1}) {
+            if (n <= 16) add(NLS_TILE_WARP, 16, r);
+            add(NLS_TILE_WARP, 32, r);
+        }
     } else if (n <= 8) {
         for (int r : {REFILL_STATIC, 0, 16, 24, 31}) add(NLS_TILE_THREAD, 0, r);
         for (int r : {REFILL_STATIC, -1}) add(NLS_TILE_WARP, 8, r);
@@ -918,7 +948,8 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
     base.maxiters = maxiters;
     Tuned best;
     for (Tuned &c : cands) {
-        KernelInfo k = ext ? nls::thread_ext_kernel(family, n, alg & NLS_ALG_MASK, mixed)
+        KernelInfo k = ext ? (c.tiles == NLS_TILE_THREAD ? nls::thread_ext_kernel(family, n, alg & NLS_ALG_MASK, mixed)
+                                                         : nls::warp_ext_kernel(family, c.lanes, alg & NLS_ALG_MASK, mixed))
                        : c.tiles == NLS_TILE_THREAD ? thread_kernel(family, n, mixed, analytic)
                        : c.tiles == NLS_TILE_WARP ? warp_kernel(family, n, mixed, c.lanes)
                                                   : cta_kernel(family, n, mixed);

@@ -451,11 +451,13 @@ constexpr int warp_smem_bytes()
     return (WARP_TPB / 32) * (32 / L) * (int)sizeof(WarpSmem<L, MIXED>);
 }
 
-template <int L, int FAM, bool MIXED>
-__global__ void __launch_bounds__(WARP_TPB) k_solve_warp(SolveArgs a)
+// The segment loop shared by the warp-tiled solvers S (r, n, lane0, status,
+// init / pass / finish): segments take instances from the work counter (or
+// the static slot), every pass runs in lock step over the whole warp.
+template <class S, int L, bool MIXED>
+NLS_DI void warp_lanes(SolveArgs &a)
 {
     apply_dyn_batch(a);
-    using S = WarpSolver<L, FAM, MIXED>;
     using SM = WarpSmem<L, MIXED>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int SEGS = 32 / L;
@@ -532,6 +534,12 @@ __global__ void __launch_bounds__(WARP_TPB) k_solve_warp(SolveArgs a)
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
         if (lane == 0 && t) atomicAdd(a.solved, t);
     }
+}
+
+template <int L, int FAM, bool MIXED>
+__global__ void __launch_bounds__(WARP_TPB) k_solve_warp(SolveArgs a)
+{
+    warp_lanes<WarpSolver<L, FAM, MIXED>, L, MIXED>(a);
 }
 
 } // namespace nls

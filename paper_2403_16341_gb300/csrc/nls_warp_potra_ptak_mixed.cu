@@ -1,0 +1,9 @@
+// Warp-tiled Potra-Ptak solver instantiations (mixed), L = 16 and 32 lanes per instance.
+#include "nls_warp_ext.cuh"
+
+namespace nls {
+KernelInfo warp_potra_ptak_mixed(int family, int L)
+{
+    return warp_ext_info_for<ALG_POTRA_PTAK, true>(family, L);
+}
+} // namespace nls

@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 
 PP, HALLEY, BROYDEN, MOD_BROYDEN = 4, 5, 6, 7
 MIXED, ANALYTIC = 1 << 8, 1 << 9
+TILE_WARP, TILE_CTA = 1 << 11, 1 << 12
 NEXT4 = (PP, HALLEY, BROYDEN, MOD_BROYDEN)
 
 
@@ -140,14 +141,14 @@ def test_unsupported_combinations(solver):
     p = torch.from_numpy(b.params).cuda()
     u = torch.from_numpy(b.u0).cuda()
     for alg in NEXT4:
-        for bad in (alg | ANALYTIC, alg | nls.NLS_TILE_WARP, alg | nls.NLS_TILE_CTA):
+        for bad in (alg | ANALYTIC, alg | nls.NLS_TILE_CTA):
             with pytest.raises(nls.NlsError) as e:
                 nls.solve(I.FAMILY_CUBIC, p, u, bad, 1e-10, 50, solver)
             assert e.value.code == nls.NLS_E_UNSUPPORTED
-    b9 = I.cubic_batch(9, 8, config_id=2)
+    b33 = I.cubic_batch(33, 8, config_id=2)
     with pytest.raises(nls.NlsError) as e:
-        nls.solve(I.FAMILY_CUBIC, torch.from_numpy(b9.params).cuda(),
-                  torch.from_numpy(b9.u0).cuda(), HALLEY, 1e-10, 50, solver)
+        nls.solve(I.FAMILY_CUBIC, torch.from_numpy(b33.params).cuda(),
+                  torch.from_numpy(b33.u0).cuda(), HALLEY, 1e-10, 50, solver)
     assert e.value.code == nls.NLS_E_UNSUPPORTED
     with pytest.raises(nls.NlsError) as e:
         nls.solve(I.FAMILY_CUBIC, p, u, 8, 1e-10, 50, solver)
@@ -187,3 +188,30 @@ def test_full_size_sampled(solver, alg):
         gs = {k: (v[..., idx] if isinstance(v, np.ndarray) else v) for k, v in g.items()}
         gs["solved"] = int((gs["status"] == 0).sum())
         check_parity(sub, gs, o, mixed, chaotic=(alg == MOD_BROYDEN))
+
+
+@pytest.mark.parametrize("family", [I.FAMILY_CUBIC, I.FAMILY_BRATU, I.FAMILY_SQUARE,
+                                    I.FAMILY_ROSENBROCK])
+@pytest.mark.parametrize("n", [9, 12, 16, 17, 24, 32])
+@pytest.mark.parametrize("alg", NEXT4)
+@pytest.mark.parametrize("mixed", [False, True])
+def test_warp_tiling(solver, family, n, alg, mixed):
+    # 8 < n <= 32: one instance per segment of 16 or 32 lanes; Rosenbrock from
+    # U[0, 1)^n is rounding-chaotic at n >= 12 for every method here (as for
+    # plain Newton at n >= 13)
+    b = family_batch(family, n, 67)
+    g = gpu_solve(solver, b, alg | (MIXED if mixed else 0))
+    o = oracle_solve(b, alg)
+    chaotic = (chaotic_case(family, alg) or (mixed and alg == BROYDEN)
+               or (family == I.FAMILY_ROSENBROCK and n >= 12))
+    check_parity(b, g, o, mixed, chaotic=chaotic)
+
+
+@pytest.mark.parametrize("alg", NEXT4)
+def test_warp_tiling_forced_small_n(solver, alg):
+    # the warp kernels also hold n <= 8 when asked to (segments of 16 lanes)
+    b = I.cubic_batch(5, 131, config_id=2)
+    g = gpu_solve(solver, b, alg | TILE_WARP)
+    o = oracle_solve(b, alg)
+    check_parity(b, g, o, False, chaotic=(alg == BROYDEN))
+
