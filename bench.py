@@ -644,29 +644,32 @@ def run_workload(args, local):
             res[name] = {"ms": ms, "solved": solved, "solved_fraction": solved / b.batch,
                          "solved_per_s": solved / (ms / 1e3)}
     elif args.workload == "next4":
-        # the higher-order, multi-step and quasi-Newton solvers on the 2^20
-        # cubic n = 8 workload, next to Newton with backtracking
-        b = I.workload_cubic_n8(args.instances)
-        dbs = _device_batches(torch, [b], dev)
-        line["config"] = (f"{b.batch} cubic n=8, A = 3I + G, b ~ U[-5,5]^8, u0 = 0; Halley "
-                          "(Eq. 3), Potra-Ptak (Eq. 4), Broyden / modified Broyden (Tab. 1), one "
-                          "thread per instance, autotuned launch")
+        # the higher-order, multi-step and quasi-Newton solvers next to Newton
+        # with backtracking: the 2^20 cubic n = 8 workload (one thread per
+        # instance) and 2^16 cubic n = 32 instances (one warp per instance)
         keep = set(args.variants.split(",")) if args.variants else None
-        _, p, u0, u, outs = dbs[0]
-        for name, alg in (("newton_backtrack", LS), ("halley", 5), ("potra_ptak", 4),
-                          ("mod_broyden", 7), ("broyden", 6)):
-            for prec, m in (("fp64", 0), ("mixed", MIXED)):
-                if keep is not None and f"{name}_{prec}" not in keep:
-                    continue
-                u.copy_(u0)
-                if not args.no_autotune:
-                    solver.autotune(b.family, p, u, alg | m, ABSTOL, MAXITERS)
-                ms, sv, nl = time_flush(torch, solver, dbs, alg | m, args.steps,
-                                        max(args.warmup, 3), stream)
-                it = outs[1][:b.batch].float()
-                res[f"{name}_{prec}"] = {"ms": ms, "solved": sv, "solved_per_s": sv / (ms / 1e3),
-                                         "mean_iters": float(it.mean().item()),
-                                         "launches": nl}
+        cases = (("", I.workload_cubic_n8(args.instances)),
+                 ("n32_", I.cubic_batch(32, 1 << 16, config_id=2)))
+        line["config"] = (f"{cases[0][1].batch} cubic n=8 (b ~ U[-5,5]^8) and 2^16 cubic n=32 "
+                          "(b ~ U[-2,2]^32), u0 = 0; Halley (Eq. 3), Potra-Ptak (Eq. 4), Broyden / "
+                          "modified Broyden (Tab. 1); thread resp. warp tiling, autotuned launch")
+        for prefix, b in cases:
+            dbs = _device_batches(torch, [b], dev)
+            _, p, u0, u, outs = dbs[0]
+            for name, alg in (("newton_backtrack", LS), ("halley", 5), ("potra_ptak", 4),
+                              ("mod_broyden", 7), ("broyden", 6)):
+                for prec, m in (("fp64", 0), ("mixed", MIXED)):
+                    key = f"{prefix}{name}_{prec}"
+                    if keep is not None and key not in keep:
+                        continue
+                    u.copy_(u0)
+                    if not args.no_autotune:
+                        solver.autotune(b.family, p, u, alg | m, ABSTOL, MAXITERS)
+                    ms, sv, nl = time_flush(torch, solver, dbs, alg | m, args.steps,
+                                            max(args.warmup, 3), stream)
+                    it = outs[1][:b.batch].float()
+                    res[key] = {"ms": ms, "solved": sv, "solved_per_s": sv / (ms / 1e3),
+                                "mean_iters": float(it.mean().item()), "launches": nl}
     elif args.workload == "tr-schemes":
         # trust-region radius updates: the Simple reading and NocedalWright
         # (Tab. 3), on the cubic n = 8 workload and on Rosenbrock n = 8 from
