@@ -60,8 +60,8 @@ enum nls_alg {
                                  backtracking, then with the trust region.
                                  iters = the final stage's passes, nfev = all
                                  stages' residual evaluations.                */
-    /* The following run one instance per thread only: n <= 8, no
-       NLS_ANALYTIC_JAC, no NLS_TILE_WARP / NLS_TILE_CTA (NLS_E_UNSUPPORTED). */
+    /* The following take forward-mode derivatives only (NLS_ANALYTIC_JAC:
+       NLS_E_UNSUPPORTED) and run on every tiling (n <= 128). */
     NLS_POTRA_PTAK = 4,       /* Sec. 2.1, Eq. 4: y = u + du1, u' = y + du2 with
                                  J(u) du1 = -F(u), J(u) du2 = -F(y) (one
                                  Jacobian and LU, two residuals per pass)     */

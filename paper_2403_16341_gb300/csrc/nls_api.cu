@@ -82,6 +82,25 @@ KernelInfo warp_ext_kernel(int family, int L, int alg, bool mixed)
     }
 }
 
+KernelInfo cta_potra_ptak_fp64(int family, int n);
+KernelInfo cta_potra_ptak_mixed(int family, int n);
+KernelInfo cta_halley_fp64(int family, int n);
+KernelInfo cta_halley_mixed(int family, int n);
+KernelInfo cta_broyden_fp64(int family, int n);
+KernelInfo cta_broyden_mixed(int family, int n);
+
+// ... and one instance per CTA (n <= 128).
+KernelInfo cta_ext_kernel(int family, int n, int alg, bool mixed)
+{
+    switch (alg) {
+    case ALG_POTRA_PTAK: return mixed ? cta_potra_ptak_mixed(family, n) : cta_potra_ptak_fp64(family, n);
+    case ALG_HALLEY: return mixed ? cta_halley_mixed(family, n) : cta_halley_fp64(family, n);
+    case ALG_BROYDEN:
+    case ALG_MOD_BROYDEN: return mixed ? cta_broyden_mixed(family, n) : cta_broyden_fp64(family, n);
+    default: return KernelInfo{};
+    }
+}
+
 KernelInfo warp_kernel_fp64(int family, int L);
 KernelInfo warp_kernel_mixed(int family, int L);
 
@@ -260,18 +279,18 @@ static int select_kernel(nls_batch *h, int family, int n, int alg, KernelInfo *o
     }
     if ((alg & NLS_ALG_MASK) >= NLS_POTRA_PTAK) {
         const int a = alg & NLS_ALG_MASK;
-        if (tiles == NLS_TILE_CTA)
-            return fail(h, NLS_E_UNSUPPORTED, "algorithm %d runs per thread or per warp segment only", a);
         if (analytic) return fail(h, NLS_E_UNSUPPORTED, "algorithm %d takes derivatives by forward mode only", a);
-        if (n > 32) return fail(h, NLS_E_UNSUPPORTED, "algorithm %d holds n <= 32 (n = %d)", a, n);
-        if (!tiles) tiles = n <= 8 ? NLS_TILE_THREAD : NLS_TILE_WARP;
+        if (!tiles) tiles = n <= 8 ? NLS_TILE_THREAD : n <= 32 ? NLS_TILE_WARP : NLS_TILE_CTA;
         if (tiles == NLS_TILE_THREAD) {
             if (n > 8) return fail(h, NLS_E_UNSUPPORTED, "thread tiling holds n <= 8 (n = %d)", n);
             *out = nls::thread_ext_kernel(family, n, a, mixed);
-        } else {
+        } else if (tiles == NLS_TILE_WARP) {
+            if (n > 32) return fail(h, NLS_E_UNSUPPORTED, "warp tiling holds n <= 32 (n = %d)", n);
             int L = (lanes == 16 || lanes == 32) && lanes >= n ? lanes : (n <= 16 ? 16 : 32);
             lanes = L;
             *out = nls::warp_ext_kernel(family, L, a, mixed);
+        } else {
+            *out = nls::cta_ext_kernel(family, n, a, mixed);
         }
     } else {
         if (!tiles) tiles = n <= 8 ? NLS_TILE_THREAD : n <= 32 ? NLS_TILE_WARP : NLS_TILE_CTA;
@@ -887,8 +906,8 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
         return fail(h, NLS_E_INVALID, "nls_autotune chooses the tiling: pass no tiling flag");
     if ((alg & NLS_ALG_MASK) == NLS_POLYALG)
         return fail(h, NLS_E_INVALID, "tune the stage algorithms, not NLS_POLYALG");
-    if ((alg & NLS_ALG_MASK) >= NLS_POTRA_PTAK && ((alg & NLS_ANALYTIC_JAC) || n > 32))
-        return fail(h, NLS_E_UNSUPPORTED, "algorithm %d: n <= 32, forward-mode derivatives", alg & NLS_ALG_MASK);
+    if ((alg & NLS_ALG_MASK) >= NLS_POTRA_PTAK && (alg & NLS_ANALYTIC_JAC))
+        return fail(h, NLS_E_UNSUPPORTED, "algorithm %d takes forward-mode derivatives only", alg & NLS_ALG_MASK);
     NLS_CUDA(h, cudaSetDevice(h->device));
     rc = flush_pending(h);
     if (rc) return rc;
@@ -925,7 +944,8 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
             for (int r : {REFILL_STATIC, 0, 16, 24, 31}) add(NLS_TILE_THREAD, 0, r);
         for (int r : {REFILL_STATIC, -1}) {
             if (n <= 16) add(NLS_TILE_WARP, 16, r);
-            add(NLS_TILE_WARP, 32, r);
+            if (n <= 32) add(NLS_TILE_WARP, 32, r);
+            if (n > 8) add(NLS_TILE_CTA, 0, r);
         }
     } else if (n <= 8) {
         for (int r : {REFILL_STATIC, 0, 16, 24, 31}) add(NLS_TILE_THREAD, 0, r);
@@ -949,7 +969,8 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
     Tuned best;
     for (Tuned &c : cands) {
         KernelInfo k = ext ? (c.tiles == NLS_TILE_THREAD ? nls::thread_ext_kernel(family, n, alg & NLS_ALG_MASK, mixed)
-                                                         : nls::warp_ext_kernel(family, c.lanes, alg & NLS_ALG_MASK, mixed))
+                              : c.tiles == NLS_TILE_WARP ? nls::warp_ext_kernel(family, c.lanes, alg & NLS_ALG_MASK, mixed)
+                                                         : nls::cta_ext_kernel(family, n, alg & NLS_ALG_MASK, mixed))
                        : c.tiles == NLS_TILE_THREAD ? thread_kernel(family, n, mixed, analytic)
                        : c.tiles == NLS_TILE_WARP ? warp_kernel(family, n, mixed, c.lanes)
                                                   : cta_kernel(family, n, mixed);

@@ -286,7 +286,12 @@ struct CtaSolver {
 #pragma unroll
                     for (int aa = 0; aa < R; ++aa) {
                         const int i = row(aa);
-                        if (i < n) sm.lcol[par][i] = (((remmask >> aa) & 1u) && i != prow_i) ? a[aa][b] * r : P(0);
+                        const bool elim = ((remmask >> aa) & 1u) && i != prow_i;
+                        const P l = a[aa][b] * r;
+                        if (i < n) sm.lcol[par][i] = elim ? l : P(0);
+                        // the multiplier stays in column kk of its row (below the
+                        // row's final position, so lu_apply finds it in sm.U)
+                        if (elim) a[aa][b] = l;
                     }
                     if (lane == src) {
                         sm.ckey[par] = kmax ? kmax - 1 : 0;
@@ -342,7 +347,8 @@ struct CtaSolver {
             }
         }
         __syncthreads();
-        // U in pivot-position order for the back substitution
+        // L \ U in pivot-position order: U on and right of each row's position
+        // (the back substitution), its multipliers left of it (lu_apply)
 #pragma unroll
         for (int aa = 0; aa < R; ++aa) {
             if (row(aa) >= n) continue;
@@ -378,6 +384,50 @@ struct CtaSolver {
         }
         __syncthreads();
         return ok;
+    }
+
+    // x = A^-1 rhs (sm.rhs by row, sm.x by column) with the factors lu_solve
+    // left in sm.U, sm.pos_row and sm.rdiag: forward substitution over the
+    // positions (the replay of the right-hand-side elimination), then the
+    // back substitution; warp 0, one shuffle broadcast per step.
+    NLS_DI void lu_apply(SM &sm) const
+    {
+        __syncthreads();
+        if (warp == 0) {
+            constexpr int J = (NM + 31) / 32;
+            P y[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int p = lane + 32 * j;
+                y[j] = p < n ? sm.rhs[sm.pos_row[p]] : P(0);
+            }
+            for (int c = 0; c < n; ++c) {
+                const int jc = c >> 5;
+                P yc = P(0);
+#pragma unroll
+                for (int j = 0; j < J; ++j) yc = (j == jc) ? y[j] : yc;
+                yc = __shfl_sync(0xffffffffu, yc, c & 31);
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const int p = lane + 32 * j;
+                    if (p > c && p < n) y[j] -= sm.U[p][c] * yc;
+                }
+            }
+            for (int kk = n - 1; kk >= 0; --kk) {
+                const int jk = kk >> 5;
+                P yk = P(0);
+#pragma unroll
+                for (int j = 0; j < J; ++j) yk = (j == jk) ? y[j] : yk;
+                const P xk = __shfl_sync(0xffffffffu, yk * sm.rdiag[kk], kk & 31);
+                if (lane == 0) sm.x[kk] = xk;
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const int p = lane + 32 * j;
+                    if (p < kk) y[j] -= sm.U[p][kk] * xk;
+                }
+            }
+        }
+        __syncthreads();
     }
 
     // ------------------------------------------------------------ driver
@@ -591,11 +641,13 @@ constexpr int cta_smem_bytes()
     return (int)sizeof(CtaSmemU<MIXED, CTA_T * R>);
 }
 
-template <int R, int FAM, bool MIXED>
-__global__ void __launch_bounds__(CTA_TPB) k_solve_cta(SolveArgs a)
+// The instance loop shared by the CTA-tiled solvers S (tid ... params set
+// here; init / pass / finish; a status): one instance per CTA at a time,
+// drawn from the work counter or the static slot.
+template <class S>
+NLS_DI void cta_loop(SolveArgs &a)
 {
     apply_dyn_batch(a);
-    using S = CtaSolver<R, FAM, MIXED>;
     using SM = typename S::SM;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SM &sm = *reinterpret_cast<SM *>(smem_raw);
@@ -639,6 +691,12 @@ __global__ void __launch_bounds__(CTA_TPB) k_solve_cta(SolveArgs a)
         }
         s.finish(a, sm);
     }
+}
+
+template <int R, int FAM, bool MIXED>
+__global__ void __launch_bounds__(CTA_TPB) k_solve_cta(SolveArgs a)
+{
+    cta_loop<CtaSolver<R, FAM, MIXED>>(a);
 }
 
 } // namespace nls

@@ -1,0 +1,9 @@
+// CTA-tiled Broyden and modified Broyden solver instantiations (fp64), register tiles R = 4 (n <= 64) and 8 (n <= 128).
+#include "nls_cta_ext.cuh"
+
+namespace nls {
+KernelInfo cta_broyden_fp64(int family, int n)
+{
+    return cta_ext_info_for<ALG_BROYDEN, false>(family, n);
+}
+} // namespace nls

@@ -1,0 +1,9 @@
+// CTA-tiled Halley solver instantiations (fp64), register tiles R = 4 (n <= 64) and 8 (n <= 128).
+#include "nls_cta_ext.cuh"
+
+namespace nls {
+KernelInfo cta_halley_fp64(int family, int n)
+{
+    return cta_ext_info_for<ALG_HALLEY, false>(family, n);
+}
+} // namespace nls

@@ -141,15 +141,16 @@ def test_unsupported_combinations(solver):
     p = torch.from_numpy(b.params).cuda()
     u = torch.from_numpy(b.u0).cuda()
     for alg in NEXT4:
-        for bad in (alg | ANALYTIC, alg | nls.NLS_TILE_CTA):
-            with pytest.raises(nls.NlsError) as e:
-                nls.solve(I.FAMILY_CUBIC, p, u, bad, 1e-10, 50, solver)
-            assert e.value.code == nls.NLS_E_UNSUPPORTED
+        with pytest.raises(nls.NlsError) as e:
+            nls.solve(I.FAMILY_CUBIC, p, u, alg | ANALYTIC, 1e-10, 50, solver)
+        assert e.value.code == nls.NLS_E_UNSUPPORTED
+    # a forced tiling that cannot hold n
     b33 = I.cubic_batch(33, 8, config_id=2)
-    with pytest.raises(nls.NlsError) as e:
-        nls.solve(I.FAMILY_CUBIC, torch.from_numpy(b33.params).cuda(),
-                  torch.from_numpy(b33.u0).cuda(), HALLEY, 1e-10, 50, solver)
-    assert e.value.code == nls.NLS_E_UNSUPPORTED
+    p33, u33 = torch.from_numpy(b33.params).cuda(), torch.from_numpy(b33.u0).cuda()
+    for bad in (HALLEY | nls.NLS_TILE_WARP, HALLEY | nls.NLS_TILE_THREAD):
+        with pytest.raises(nls.NlsError) as e:
+            nls.solve(I.FAMILY_CUBIC, p33, u33, bad, 1e-10, 50, solver)
+        assert e.value.code == nls.NLS_E_UNSUPPORTED
     with pytest.raises(nls.NlsError) as e:
         nls.solve(I.FAMILY_CUBIC, p, u, 8, 1e-10, 50, solver)
     assert e.value.code == nls.NLS_E_INVALID
@@ -214,6 +215,31 @@ def test_warp_tiling_forced_small_n(solver, alg):
     # the warp kernels also hold n <= 8 when asked to (segments of 16 lanes)
     b = I.cubic_batch(5, 131, config_id=2)
     g = gpu_solve(solver, b, alg | TILE_WARP)
+    o = oracle_solve(b, alg)
+    check_parity(b, g, o, False, chaotic=(alg == BROYDEN))
+
+
+@pytest.mark.parametrize("family", [I.FAMILY_CUBIC, I.FAMILY_BRATU, I.FAMILY_SQUARE])
+@pytest.mark.parametrize("n", [33, 40, 64, 65, 100, 128])
+@pytest.mark.parametrize("alg", NEXT4)
+@pytest.mark.parametrize("mixed", [False, True])
+def test_cta_tiling(solver, family, n, alg, mixed):
+    # 32 < n <= 128: one instance per CTA (register tiles R = 4 or 8); the
+    # oracle solves every instance with Potra-Ptak, Halley and modified
+    # Broyden and none with Broyden from B_0 = I
+    b = family_batch(family, n, 37)
+    g = gpu_solve(solver, b, alg | (MIXED if mixed else 0))
+    o = oracle_solve(b, alg)
+    check_parity(b, g, o, mixed, chaotic=(alg == BROYDEN))
+    if alg != BROYDEN:
+        assert g["solved"] == b.batch
+
+
+@pytest.mark.parametrize("alg", NEXT4)
+def test_cta_tiling_forced_small_n(solver, alg):
+    # the CTA kernels also hold small n when asked to
+    b = I.cubic_batch(12, 45, config_id=2)
+    g = gpu_solve(solver, b, alg | TILE_CTA)
     o = oracle_solve(b, alg)
     check_parity(b, g, o, False, chaotic=(alg == BROYDEN))
 
