@@ -646,13 +646,16 @@ def run_workload(args, local):
     elif args.workload == "next4":
         # the higher-order, multi-step and quasi-Newton solvers next to Newton
         # with backtracking: the 2^20 cubic n = 8 workload (one thread per
-        # instance) and 2^16 cubic n = 32 instances (one warp per instance)
+        # instance), 2^16 cubic n = 32 (one warp per instance) and 2^14 cubic
+        # n = 64 (one CTA per instance)
         keep = set(args.variants.split(",")) if args.variants else None
         cases = (("", I.workload_cubic_n8(args.instances)),
-                 ("n32_", I.cubic_batch(32, 1 << 16, config_id=2)))
-        line["config"] = (f"{cases[0][1].batch} cubic n=8 (b ~ U[-5,5]^8) and 2^16 cubic n=32 "
-                          "(b ~ U[-2,2]^32), u0 = 0; Halley (Eq. 3), Potra-Ptak (Eq. 4), Broyden / "
-                          "modified Broyden (Tab. 1); thread resp. warp tiling, autotuned launch")
+                 ("n32_", I.cubic_batch(32, 1 << 16, config_id=2)),
+                 ("n64_", I.cubic_batch(64, 1 << 14, config_id=2)))
+        line["config"] = (f"{cases[0][1].batch} cubic n=8 (b ~ U[-5,5]^8), 2^16 cubic n=32 and 2^14 "
+                          "cubic n=64 (b ~ U[-2,2]^n), u0 = 0; Halley (Eq. 3), Potra-Ptak (Eq. 4), "
+                          "Broyden / modified Broyden (Tab. 1); thread, warp and CTA tiling, "
+                          "autotuned launch")
         for prefix, b in cases:
             dbs = _device_batches(torch, [b], dev)
             _, p, u0, u, outs = dbs[0]

@@ -386,46 +386,54 @@ struct CtaSolver {
         return ok;
     }
 
-    // x = A^-1 rhs (sm.rhs by row, sm.x by column) with the factors lu_solve
-    // left in sm.U, sm.pos_row and sm.rdiag: forward substitution over the
-    // positions (the replay of the right-hand-side elimination), then the
-    // back substitution; warp 0, one shuffle broadcast per step.
+    // One warp's solve with the factors lu_solve left in sm.U (multipliers
+    // left of each row's position, U from it on), sm.pos_row and sm.rdiag:
+    // y holds the right-hand side by position (lane l: positions l, l + 32,
+    // ...); forward substitution over the positions (the replay of the
+    // right-hand-side elimination), then the back substitution, one shuffle
+    // broadcast per step; x (by column) goes to xout.  Warp-synchronous.
+    static constexpr int YJ = (NM + 31) / 32;
+    NLS_DI void lu_apply_warp(const SM &sm, P (&y)[YJ], P *xout) const
+    {
+        for (int c = 0; c < n; ++c) {
+            const int jc = c >> 5;
+            P yc = P(0);
+#pragma unroll
+            for (int j = 0; j < YJ; ++j) yc = (j == jc) ? y[j] : yc;
+            yc = __shfl_sync(0xffffffffu, yc, c & 31);
+#pragma unroll
+            for (int j = 0; j < YJ; ++j) {
+                const int p = lane + 32 * j;
+                if (p > c && p < n) y[j] -= sm.U[p][c] * yc;
+            }
+        }
+        for (int kk = n - 1; kk >= 0; --kk) {
+            const int jk = kk >> 5;
+            P yk = P(0);
+#pragma unroll
+            for (int j = 0; j < YJ; ++j) yk = (j == jk) ? y[j] : yk;
+            const P xk = __shfl_sync(0xffffffffu, yk * sm.rdiag[kk], kk & 31);
+            if (lane == 0) xout[kk] = xk;
+#pragma unroll
+            for (int j = 0; j < YJ; ++j) {
+                const int p = lane + 32 * j;
+                if (p < kk) y[j] -= sm.U[p][kk] * xk;
+            }
+        }
+    }
+
+    // x = A^-1 rhs (sm.rhs by row, sm.x by column) on warp 0.
     NLS_DI void lu_apply(SM &sm) const
     {
         __syncthreads();
         if (warp == 0) {
-            constexpr int J = (NM + 31) / 32;
-            P y[J];
+            P y[YJ];
 #pragma unroll
-            for (int j = 0; j < J; ++j) {
+            for (int j = 0; j < YJ; ++j) {
                 const int p = lane + 32 * j;
                 y[j] = p < n ? sm.rhs[sm.pos_row[p]] : P(0);
             }
-            for (int c = 0; c < n; ++c) {
-                const int jc = c >> 5;
-                P yc = P(0);
-#pragma unroll
-                for (int j = 0; j < J; ++j) yc = (j == jc) ? y[j] : yc;
-                yc = __shfl_sync(0xffffffffu, yc, c & 31);
-#pragma unroll
-                for (int j = 0; j < J; ++j) {
-                    const int p = lane + 32 * j;
-                    if (p > c && p < n) y[j] -= sm.U[p][c] * yc;
-                }
-            }
-            for (int kk = n - 1; kk >= 0; --kk) {
-                const int jk = kk >> 5;
-                P yk = P(0);
-#pragma unroll
-                for (int j = 0; j < J; ++j) yk = (j == jk) ? y[j] : yk;
-                const P xk = __shfl_sync(0xffffffffu, yk * sm.rdiag[kk], kk & 31);
-                if (lane == 0) sm.x[kk] = xk;
-#pragma unroll
-                for (int j = 0; j < J; ++j) {
-                    const int p = lane + 32 * j;
-                    if (p < kk) y[j] -= sm.U[p][kk] * xk;
-                }
-            }
+            lu_apply_warp(sm, y, sm.x);
         }
         __syncthreads();
     }

@@ -12,7 +12,7 @@
 //    Newton kernels; products with vectors reduce the threads' partial sums
 //    through shared memory (the tiling's J^T F pattern), and the rank-one
 //    update touches each tile once.  Modified Broyden's start J(u_0)^-1 is
-//    filled one column per solve.
+//    solved eight columns at a time, one unit vector per warp.
 #pragma once
 
 #include "nls_cta.cuh"
@@ -216,18 +216,30 @@ struct CtaSolverBroyden : CtaSolverExtBase<R, FAM, MIXED> {
                 for (int aa = 0; aa < R; ++aa)
 #pragma unroll
                     for (int bb = 0; bb < R; ++bb) H[aa][bb] = P(0);
-                // column j of J^-1 per solve; its owners (tx == j mod 16) keep it
-                for (int j = 0; j < n; ++j) {
-                    if (own) sm.rhs[t] = (t == j) ? P(1) : P(0);
-                    this->lu_apply(sm);
-                    const int bj = j / CTA_T;
-                    if (tx == (j & (CTA_T - 1))) {
+                // J^-1 eight columns at a time: warp w solves for unit vector
+                // j0 + w into row w of the partial-sum buffer, then the owners
+                // of those columns copy them into their tiles
+                constexpr int W = CTA_TPB / 32;
+                for (int j0 = 0; j0 < n; j0 += W) {
+                    const int j = j0 + this->warp;
+                    if (j < n) {
+                        P y[Bx::YJ];
 #pragma unroll
-                        for (int aa = 0; aa < R; ++aa)
-#pragma unroll
-                            for (int bb = 0; bb < R; ++bb)
-                                if (bb == bj && this->row(aa) < n) H[aa][bb] = sm.x[this->row(aa)];
+                        for (int q = 0; q < Bx::YJ; ++q) {
+                            const int p = this->lane + 32 * q;
+                            y[q] = (p < n && sm.pos_row[p] == j) ? P(1) : P(0);
+                        }
+                        this->lu_apply_warp(sm, y, sm.red[this->warp]);
                     }
+                    __syncthreads();
+#pragma unroll
+                    for (int aa = 0; aa < R; ++aa)
+#pragma unroll
+                        for (int bb = 0; bb < R; ++bb) {
+                            const int c = this->col(bb);
+                            if (c >= j0 && c < j0 + W && c < n && this->row(aa) < n)
+                                H[aa][bb] = sm.red[c - j0][this->row(aa)];
+                        }
                     __syncthreads();
                 }
             } else {
