@@ -54,12 +54,16 @@ enum nls_alg {
     NLS_NEWTON = 0,           /* Sec. 2.1, Eq. 2                               */
     NLS_NEWTON_BACKTRACK = 1, /* Sec. 2.2.1: Armijo (Eq. 8-9), alpha <- alpha/2 */
     NLS_TRUST_DOGLEG = 2,     /* Sec. 2.2.2: Eq. 12-14, Powell's dogleg          */
-    NLS_POLYALG = 3,          /* Sec. 3.2 poly-algorithm for n <= 25 (no quasi-
-                                 Newton stage): Newton on every instance; the
-                                 ones that fail restart from u0 with
-                                 backtracking, then with the trust region.
-                                 iters = the final stage's passes, nfev = all
-                                 stages' residual evaluations.                */
+    NLS_POLYALG = 3,          /* Sec. 3.2 poly-algorithm: the first stage runs
+                                 on every instance, the ones that fail
+                                 restart from u0 with the next stage.  n > 25:
+                                 Broyden, modified Broyden (the quasi-Newton
+                                 phase; Klement is not built), Newton,
+                                 backtracking, trust region; n <= 25: Newton,
+                                 backtracking, trust region (the paper skips
+                                 quasi-Newton there).  iters = the final
+                                 stage's passes, nfev = all stages' residual
+                                 evaluations.                                 */
     /* The following take forward-mode derivatives only (NLS_ANALYTIC_JAC:
        NLS_E_UNSUPPORTED) and run on every tiling (n <= 128). */
     NLS_POTRA_PTAK = 4,       /* Sec. 2.1, Eq. 4: y = u + du1, u' = y + du2 with

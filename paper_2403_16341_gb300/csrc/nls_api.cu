@@ -140,7 +140,8 @@ struct Request {
     SolveArgs args{};
     KernelInfo kern{};
     int family = 0, tiles = 0, lanes = 0, refill = -1;
-    bool poly = false;             // NLS_POLYALG: Newton, then backtracking, then trust region
+    int alg_flags = 0;             // the alg word as submitted (precision and tiling flags)
+    bool poly = false;             // NLS_POLYALG: the stages of launch_poly
     void *poly_ws = nullptr;       // its device workspace (freed at completion)
     size_t poly_bytes = 0;
     double rate = 0.0;                     // tuned rate (0 = use the cost model)
@@ -496,11 +497,18 @@ static int launch_direct(nls_batch *h, const std::vector<Request *> &rs, const s
 // Device workspace of a poly-algorithm request: the original u0, compact
 // copies of the instances still failing, their outputs, full-size outputs the
 // caller did not provide, and the stage counters.
+// Stages of the poly-algorithm (Sec. 3.2, Fig. 4): a quasi-Newton phase
+// (Broyden, then modified Broyden; Klement is not built) for n > 25, then
+// Newton, backtracking, trust region.  For n <= 25 the quasi-Newton phase
+// is skipped, as in the paper.
+constexpr int POLY_MAX_STAGES = 5;
+constexpr int POLY_QN_MIN_N = 26;
+
 struct PolyWs {
     double *u0, *cparams, *cu, *cres, *fres;
     int64_t *idx;
     int32_t *cst, *cit, *cnf, *fst, *fit, *fnf;
-    unsigned long long *ctr; // [0..2] stage 2: gathered, solved, work; [3..5] stage 3
+    unsigned long long *ctr; // per gathered stage s: [3s] gathered, [3s+1] solved, [3s+2] work
 };
 
 static size_t poly_layout(int64_t B, int n, int E, char *base, PolyWs *w)
@@ -525,7 +533,7 @@ static size_t poly_layout(int64_t B, int n, int E, char *base, PolyWs *w)
     t.fst = (int32_t *)take((size_t)B * 4);
     t.fit = (int32_t *)take((size_t)B * 4);
     t.fnf = (int32_t *)take((size_t)B * 4);
-    t.ctr = (unsigned long long *)take(8 * 8);
+    t.ctr = (unsigned long long *)take(POLY_MAX_STAGES * 3 * 8);
     if (w) *w = t;
     return off;
 }
@@ -537,6 +545,7 @@ static int launch_poly(nls_batch *h, Request &r)
 {
     const int64_t B = r.args.batch;
     const int n = r.args.n, E = n_params(r.family, n);
+    const bool mixed = (r.alg_flags & NLS_MIXED) != 0;
     PolyWs w;
     poly_layout(B, n, E, static_cast<char *>(r.poly_ws), &w);
     cudaStream_t st = h->stream;
@@ -546,21 +555,40 @@ static int launch_poly(nls_batch *h, Request &r)
     if (!a.nfev) a.nfev = w.fnf;
     if (!a.resid) a.resid = w.fres;
     NLS_CUDA(h, cudaMemcpyAsync(w.u0, a.u, (size_t)n * B * 8, cudaMemcpyDeviceToDevice, st));
-    NLS_CUDA(h, cudaMemsetAsync(w.ctr, 0, 8 * 8, st));
-    a.alg = NLS_NEWTON;
+    NLS_CUDA(h, cudaMemsetAsync(w.ctr, 0, POLY_MAX_STAGES * 3 * 8, st));
+    int stages[POLY_MAX_STAGES], ns = 0;
+    if (n >= POLY_QN_MIN_N) {
+        stages[ns++] = NLS_BROYDEN;
+        stages[ns++] = NLS_MOD_BROYDEN;
+    }
+    stages[ns++] = NLS_NEWTON;
+    stages[ns++] = NLS_NEWTON_BACKTRACK;
+    stages[ns++] = NLS_TRUST_DOGLEG;
+    // the kernel of a stage: the request's tiling; Broyden's on the same tiling
+    auto stage_kernel = [&](int alg) -> KernelInfo {
+        if (alg < NLS_BROYDEN) return r.kern;
+        if (r.tiles == NLS_TILE_WARP) return nls::warp_ext_kernel(r.family, n <= 16 ? 16 : 32, alg, mixed);
+        return nls::cta_ext_kernel(r.family, n, alg, mixed);
+    };
+    // first stage on the whole batch
+    KernelInfo k0 = stage_kernel(stages[0]);
+    if (!k0.launch) return fail(h, NLS_E_UNSUPPORTED, "no poly stage kernel for family %d, n = %d", r.family, n);
+    a.alg = stages[0];
     a.counter = nullptr;
     a.refill_below = 0;
-    const int64_t ctas = (B + r.kern.per_cta - 1) / r.kern.per_cta;
-    cudaError_t e = r.kern.launch(a, (int)std::min<int64_t>(ctas, INT32_MAX), st);
+    const int64_t ctas0 = (B + k0.per_cta - 1) / k0.per_cta;
+    cudaError_t e = k0.launch(a, (int)std::min<int64_t>(ctas0, INT32_MAX), st);
     if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "poly stage 1: %s", cudaGetErrorString(e));
     ++h->launches;
-    int occ = 0;
-    int rc = occupancy(h, r.kern, &occ);
-    if (rc) return rc;
-    const int grid = (int)std::min<int64_t>(ctas, (int64_t)std::max(occ, 1) * h->sms);
-    const int stages[2] = {NLS_NEWTON_BACKTRACK, NLS_TRUST_DOGLEG};
-    for (int sidx = 0; sidx < 2; ++sidx) {
-        unsigned long long *cnt = w.ctr + 3 * sidx;
+    for (int sidx = 1; sidx < ns; ++sidx) {
+        const KernelInfo ks = stage_kernel(stages[sidx]);
+        if (!ks.launch) return fail(h, NLS_E_UNSUPPORTED, "no poly stage kernel for family %d, n = %d", r.family, n);
+        int occ = 0;
+        int rc = occupancy(h, ks, &occ);
+        if (rc) return rc;
+        const int64_t ctas = (B + ks.per_cta - 1) / ks.per_cta;
+        const int grid = (int)std::min<int64_t>(ctas, (int64_t)std::max(occ, 1) * h->sms);
+        unsigned long long *cnt = w.ctr + 3 * (sidx - 1);
         nls::PolyGatherArgs g{B, E, n, a.status, a.params, w.u0, w.idx, w.cparams, w.cu, cnt};
         e = nls::launch_poly_gather(g, st);
         if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "poly gather: %s", cudaGetErrorString(e));
@@ -578,15 +606,15 @@ static int launch_poly(nls_batch *h, Request &r)
         c.solved = cnt + 1;
         c.counter = cnt + 2;
         c.refill_below = h->opt.refill_below;
-        e = r.kern.launch(c, grid, st);
-        if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "poly stage %d: %s", sidx + 2, cudaGetErrorString(e));
+        e = ks.launch(c, grid, st);
+        if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "poly stage %d: %s", sidx + 1, cudaGetErrorString(e));
         nls::PolyScatterArgs sc{B, n, cnt, w.idx, w.cu, w.cst, w.cit, w.cnf, w.cres,
                                 a.u, a.status, a.iters, a.nfev, a.resid};
         e = nls::launch_poly_scatter(sc, st);
         if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "poly scatter: %s", cudaGetErrorString(e));
         h->launches += 3;
     }
-    e = nls::launch_poly_total(a.solved, w.ctr + 1, w.ctr + 4, st);
+    e = nls::launch_poly_total(a.solved, w.ctr, ns - 1, st);
     if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "poly total: %s", cudaGetErrorString(e));
     ++h->launches;
     return NLS_OK;
@@ -765,6 +793,7 @@ int nls_solve(nls_handle h, int family, const double *params, double *u, int n, 
     r.args.ld = batch;
     r.args.n = n;
     r.args.alg = alg & NLS_ALG_MASK;
+    r.alg_flags = alg;
     r.args.tr_scheme = (alg & NLS_TR_NOCEDAL_WRIGHT) ? nls::TR_NOCEDAL_WRIGHT : nls::TR_SIMPLE;
     r.args.abstol = abstol;
     r.args.maxiters = maxiters;

@@ -72,6 +72,9 @@ struct PolyScatterArgs {
 };
 cudaError_t launch_poly_gather(const PolyGatherArgs &g, cudaStream_t st);
 cudaError_t launch_poly_scatter(const PolyScatterArgs &s, cudaStream_t st);
-cudaError_t launch_poly_total(unsigned long long *solved, const unsigned long long *s2,
-                              const unsigned long long *s3, cudaStream_t st);
+cudaError_t launch_poly_total(unsigned long long *solved, const unsigned long long *ctr, int stages,
+                              cudaStream_t st);
+// stage kernels of the poly-algorithm's quasi-Newton phase
+KernelInfo warp_ext_kernel(int family, int L, int alg, bool mixed);
+KernelInfo cta_ext_kernel(int family, int n, int alg, bool mixed);
 } // namespace nls

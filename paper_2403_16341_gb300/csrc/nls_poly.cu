@@ -1,6 +1,6 @@
-// nls_poly.cu -- device side of the batched poly-algorithm (Sec. 3.2): after
-// a stage, the instances that did not converge are gathered (with their
-// original u0) into compact arrays, solved by the next, more robust
+// nls_poly.cu -- device side of the batched poly-algorithm (Sec. 3.2, Fig. 4):
+// after a stage, the instances that did not converge are gathered (with
+// their original u0) into compact arrays, solved by the next, more robust
 // algorithm, and scattered back.  Counts stay on the device: the next
 // stage's kernels read them (SolveArgs::dyn_batch).
 #include <cuda_runtime.h>
@@ -31,10 +31,13 @@ __global__ void k_poly_scatter(PolyScatterArgs s)
     s.nfev[k] += s.cnfev[pos]; // residual evaluations of every stage
 }
 
-__global__ void k_poly_total(unsigned long long *solved, const unsigned long long *s2,
-                             const unsigned long long *s3)
+// solved += the solved counts of the gathered stages (counter triples:
+// gathered, solved, work)
+__global__ void k_poly_total(unsigned long long *solved, const unsigned long long *ctr, int stages)
 {
-    *solved += *s2 + *s3;
+    unsigned long long t = 0;
+    for (int s = 0; s < stages; ++s) t += ctr[3 * s + 1];
+    *solved += t;
 }
 
 cudaError_t launch_poly_gather(const PolyGatherArgs &g, cudaStream_t st)
@@ -51,10 +54,10 @@ cudaError_t launch_poly_scatter(const PolyScatterArgs &s, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_poly_total(unsigned long long *solved, const unsigned long long *s2,
-                              const unsigned long long *s3, cudaStream_t st)
+cudaError_t launch_poly_total(unsigned long long *solved, const unsigned long long *ctr, int stages,
+                              cudaStream_t st)
 {
-    k_poly_total<<<1, 1, 0, st>>>(solved, s2, s3);
+    k_poly_total<<<1, 1, 0, st>>>(solved, ctr, stages);
     return cudaGetLastError();
 }
 

@@ -82,3 +82,55 @@ def test_poly_warp_and_cta_tilings(solver, n, floor):
     assert ok.mean() >= floor - 1e-12 and ok.sum() > (nr["status"] == 0).sum()
     np.testing.assert_allclose(g["u"][:, ok], 1.0, atol=1e-7)
     assert (g["resid"][ok] <= 1e-10).all()
+
+
+def oracle_chain(b, algs, abstol=1e-10, maxiters=50):
+    u, st, it, rs, nf = O.solve_batch(b.family, b.params, b.u0, algs[0], abstol, maxiters)
+    nf = nf.copy()
+    for alg in algs[1:]:
+        bad = np.nonzero(st != O.ST_SUCCESS)[0]
+        if bad.size == 0:
+            break
+        P = b.params[:, bad] if b.params.size else np.zeros((0, bad.size))
+        u2, st2, it2, rs2, nf2 = O.solve_batch(b.family, P, b.u0[:, bad], alg, abstol, maxiters)
+        u[:, bad], st[bad], it[bad] = u2, st2, it2
+        nf[bad] += nf2
+    return u, st, it, nf
+
+
+@pytest.mark.parametrize("family,n", [(I.FAMILY_CUBIC, 30), (I.FAMILY_CUBIC, 40),
+                                      (I.FAMILY_BRATU, 64), (I.FAMILY_SQUARE, 100)])
+@pytest.mark.parametrize("mixed", [False, True])
+def test_poly_quasi_newton_phase(solver, family, n, mixed):
+    # n > 25: Broyden, modified Broyden, then the Newton stages (Sec. 3.2);
+    # from these starts Broyden with B_0 = I solves (almost) nothing, the
+    # modified Broyden stage everything that is left
+    B = 97
+    b = (I.cubic_batch(n, B, config_id=2) if family == I.FAMILY_CUBIC else
+         I.bratu_batch(n, B, config_id=2) if family == I.FAMILY_BRATU else I.square_batch(n, B))
+    g = gpu_solve(solver, b, POLY | (1 << 8 if mixed else 0))
+    chain = (O.ALG_BROYDEN, O.ALG_MOD_BROYDEN, O.ALG_NEWTON, O.ALG_NEWTON_BACKTRACK,
+             O.ALG_TRUST_DOGLEG)
+    ou, ost, oit, onf = oracle_chain(b, chain)
+    assert (ost == 0).all() and (g["status"] == 0).all() and g["solved"] == B
+    ref = O.polish_batch(b.family, b.params, ou)
+    err = np.abs(g["u"] - ref).max(axis=0) / np.maximum(1.0, np.abs(ref).max(axis=0))
+    assert err.max() <= (1e-8 if mixed else 1e-9)
+    # every instance ran the Broyden stage first: more residuals than its own
+    # final stage's passes account for
+    assert (g["nfev"] > g["iters"] + 1).all()
+    if not mixed:
+        # the instances the Broyden stage left to modified Broyden agree with
+        # the oracle composition's pass counts almost everywhere
+        assert (g["iters"] == oit).mean() > 0.9
+
+
+def test_poly_skips_quasi_newton_at_25(solver):
+    # n = 25: no quasi-Newton phase, the result is plain Newton's where it converges
+    b = I.cubic_batch(25, 97, config_id=2)
+    nr = gpu_solve(solver, b, 0)
+    assert (nr["status"] == 0).all()
+    g = gpu_solve(solver, b, POLY)
+    for key in ("u", "status", "iters", "nfev"):
+        np.testing.assert_array_equal(g[key], nr[key])
+
