@@ -617,32 +617,37 @@ def run_workload(args, local):
                          "hbm_gbs": bytes_moved / (ms / 1e3) / 1e9,
                          "singular": int((st != 0).sum().item())}
     elif args.workload == "poly":
-        # Rosenbrock n = 8 from the Sec. 3.3 starts, every third moved to the
-        # Fig. 1 start where plain Newton fails
+        # (1) Rosenbrock n = 8 from the Sec. 3.3 starts, every third moved to
+        # the Fig. 1 start where plain Newton fails; (2) 2^14 cubic n = 40,
+        # where the poly-algorithm opens with its quasi-Newton phase
         b = I.rosenbrock_batch(8, 1 << 18, seed=0)
         b.u0[0, ::3] = -1.2
         b.u0[1:, ::3] = 1.0
-        dbs = _device_batches(torch, [b], dev)
+        b40 = I.cubic_batch(40, 1 << 14, config_id=2)
         line["config"] = ("2^18 generalized Rosenbrock n=8, u0 ~ U[0,1)^8 with every third "
-                          "at (-1.2, 1, ..., 1); maxiters 300")
-        for name, alg in (("newton", NEWTON), ("poly", 3), ("poly_mixed", 3 | MIXED)):
-            times, solved = [], 0
-            for r in range(max(args.warmup, 3) + args.steps):
-                _, p, u0, u, outs = dbs[0]
-                u.copy_(u0)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                q = solver.submit(b.family, None, u, alg, ABSTOL, 300, outs)
-                solver.flush()
-                e1.record(stream)
-                sv = solver.wait(q)
-                torch.cuda.synchronize()
-                if r >= max(args.warmup, 3):
-                    times.append(e0.elapsed_time(e1))
-                    solved = sv
-            ms = float(np.median(times))
-            res[name] = {"ms": ms, "solved": solved, "solved_fraction": solved / b.batch,
-                         "solved_per_s": solved / (ms / 1e3)}
+                          "at (-1.2, 1, ..., 1), maxiters 300; 2^14 cubic n=40 (b ~ U[-2,2]^40), "
+                          "maxiters 50")
+        for prefix, bb, mi in (("", b, 300), ("n40_", b40, MAXITERS)):
+            dbs = _device_batches(torch, [bb], dev)
+            for name, alg in (("newton", NEWTON), ("poly", 3), ("poly_mixed", 3 | MIXED)):
+                times, solved, iters = [], 0, 0.0
+                for r in range(max(args.warmup, 3) + args.steps):
+                    _, p, u0, u, outs = dbs[0]
+                    u.copy_(u0)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    q = solver.submit(bb.family, p, u, alg, ABSTOL, mi, outs)
+                    solver.flush()
+                    e1.record(stream)
+                    sv = solver.wait(q)
+                    torch.cuda.synchronize()
+                    if r >= max(args.warmup, 3):
+                        times.append(e0.elapsed_time(e1))
+                        solved = sv
+                        iters = float(outs[3][:bb.batch].float().mean().item())
+                ms = float(np.median(times))
+                res[prefix + name] = {"ms": ms, "solved": solved, "solved_fraction": solved / bb.batch,
+                                      "solved_per_s": solved / (ms / 1e3), "mean_nfev": iters}
     elif args.workload == "next4":
         # the higher-order, multi-step and quasi-Newton solvers next to Newton
         # with backtracking: the 2^20 cubic n = 8 workload (one thread per
