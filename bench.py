@@ -442,9 +442,14 @@ def run_ours(args, world, rank, local):
         threads = os.cpu_count() or 1
         sample = min(B, args.sample)
         rate, dt, _ = oracle_rate(batch, threads, sample)
+        # and on one core, over a smaller sample
+        rate1, dt1, _ = oracle_rate(batch, 1, min(sample, 1 << 14))
         cpu = {"value": rate, "unit": "solved systems/s", "cores": threads, "kind": "oracle",
                "sample": f"first {sample} of the 2^20 instances, NR+backtracking and TR-dogleg "
-                         f"in FP64 ({dt:.1f} s)"}
+                         f"in FP64 ({dt:.1f} s on {threads} threads)",
+               "single_thread_value": rate1,
+               "single_thread_sample": f"first {min(sample, 1 << 14)} instances, both "
+                                       f"algorithms, 1 thread ({dt1:.1f} s)"}
 
     traffic = dram_traffic(dom)
     achieved = dv["fp64_tflops"]
@@ -734,7 +739,7 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--sample", type=int, default=1 << 18,
+    ap.add_argument("--sample", type=int, default=1 << 20,
                     help="instances the CPU oracle solves per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", default="",

@@ -995,20 +995,51 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
     base.tr_scheme = (alg & NLS_TR_NOCEDAL_WRIGHT) ? nls::TR_NOCEDAL_WRIGHT : nls::TR_SIMPLE;
     base.abstol = abstol;
     base.maxiters = maxiters;
+    // the kernel of a candidate tiling
+    auto cand_kernel = [&](const Tuned &c) -> KernelInfo {
+        const int a = alg & NLS_ALG_MASK;
+        if (ext)
+            return c.tiles == NLS_TILE_THREAD ? nls::thread_ext_kernel(family, n, a, mixed)
+                   : c.tiles == NLS_TILE_WARP ? nls::warp_ext_kernel(family, c.lanes, a, mixed)
+                                              : nls::cta_ext_kernel(family, n, a, mixed);
+        return c.tiles == NLS_TILE_THREAD ? thread_kernel(family, n, mixed, analytic)
+               : c.tiles == NLS_TILE_WARP ? warp_kernel(family, n, mixed, c.lanes)
+                                          : cta_kernel(family, n, mixed);
+    };
     Tuned best;
     for (Tuned &c : cands) {
-        KernelInfo k = ext ? (c.tiles == NLS_TILE_THREAD ? nls::thread_ext_kernel(family, n, alg & NLS_ALG_MASK, mixed)
-                              : c.tiles == NLS_TILE_WARP ? nls::warp_ext_kernel(family, c.lanes, alg & NLS_ALG_MASK, mixed)
-                                                         : nls::cta_ext_kernel(family, n, alg & NLS_ALG_MASK, mixed))
-                       : c.tiles == NLS_TILE_THREAD ? thread_kernel(family, n, mixed, analytic)
-                       : c.tiles == NLS_TILE_WARP ? warp_kernel(family, n, mixed, c.lanes)
-                                                  : cta_kernel(family, n, mixed);
+        KernelInfo k = cand_kernel(c);
         if (!k.launch) continue;
         float ms = 0.f;
         rc = tune_trial(h, base, k, c.refill, save, S, ctr, &ms);
         if (rc) return rc;
         c.rate = double(S) / (double(ms) * 1e-3);
         if (c.rate > best.rate) best = c;
+    }
+    // a close final (within 5%) is decided again: the two leaders alternate
+    // for three more best-of-3 rounds, so a drift of the clock or a noisy
+    // first trial does not pick the slower launch mode
+    {
+        std::vector<Tuned *> order;
+        for (Tuned &c : cands)
+            if (c.rate > 0.0) order.push_back(&c);
+        std::sort(order.begin(), order.end(), [](const Tuned *x, const Tuned *y) { return x->rate > y->rate; });
+        if (order.size() >= 2 && order[1]->rate > 0.95 * order[0]->rate) {
+            Tuned *fin[2] = {order[0], order[1]};
+            float bestms[2] = {1e30f, 1e30f};
+            for (int round = 0; round < 3; ++round) {
+                for (int f = 0; f < 2; ++f) {
+                    const Tuned &c = *fin[f];
+                    KernelInfo k = cand_kernel(c);
+                    float ms = 0.f;
+                    rc = tune_trial(h, base, k, c.refill, save, S, ctr, &ms);
+                    if (rc) return rc;
+                    bestms[f] = std::min(bestms[f], ms);
+                }
+            }
+            for (int f = 0; f < 2; ++f) fin[f]->rate = double(S) / (double(bestms[f]) * 1e-3);
+            best = fin[0]->rate >= fin[1]->rate ? *fin[0] : *fin[1];
+        }
     }
     NLS_CUDA(h, cudaMemcpy2DAsync(u, batch * 8, save, S * 8, S * 8, n, cudaMemcpyDeviceToDevice, h->stream));
     NLS_CUDA(h, cudaStreamSynchronize(h->stream));
