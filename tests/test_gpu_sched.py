@@ -131,3 +131,30 @@ def test_uneven_full_size(solver, mixed):
         err = np.abs(u[:, idx] - ref).max(axis=0) / np.maximum(1, np.abs(ref).max(axis=0))
         assert err.max() <= (1e-8 if mixed else 1e-9)
     assert total == 1 << 18
+
+
+@pytest.mark.parametrize("n,alg", [(6, 5), (12, 5), (40, 4), (24, 7)])
+def test_autotune_next4_algorithms(solver, n, alg, tmp_path):
+    # Halley, Potra-Ptak and modified Broyden: the tuner picks among the
+    # tilings that hold n and the solve it then runs matches the oracle
+    import torch
+    import paper_2403_16341_gb300 as nls
+    b = I.cubic_batch(n, 2048, config_id=7)
+    p = torch.from_numpy(b.params).cuda()
+    u = torch.from_numpy(b.u0).cuda()
+    tiles = solver.autotune(b.family, p, u, alg | MIXED)
+    assert tiles in {nls.NLS_TILE_THREAD, nls.NLS_TILE_WARP, nls.NLS_TILE_CTA}
+    if n > 8:
+        assert tiles != nls.NLS_TILE_THREAD
+    if n > 32:
+        assert tiles == nls.NLS_TILE_CTA
+    g = gpu_solve(solver, b, alg | MIXED)
+    check_parity(b, g, oracle_solve(b, alg), mixed=True)
+    path = str(tmp_path / "tune.txt")
+    nls.nls_tune_save(solver.h, path)
+    s2 = nls.Solver(0)
+    nls.nls_tune_load(s2.h, path)
+    g2 = gpu_solve(s2, b, alg | MIXED)
+    s2.close()
+    np.testing.assert_array_equal(g2["u"], g["u"])
+

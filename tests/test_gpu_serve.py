@@ -50,7 +50,12 @@ def request_bytes(b):
     return al(b.params.size * 8) + al(b.u0.size * 8) + al(b.batch * 8) + 3 * al(b.batch * 4)
 
 
-@pytest.mark.parametrize("alg", [LS | MIXED, TR])
+HALLEY, NW = 5, 1 << 13
+
+
+# Halley runs on the thread tiling for n <= 8 and on warp segments for 16 and
+# 32; the NocedalWright flag rides along with the trust region
+@pytest.mark.parametrize("alg", [LS | MIXED, TR, HALLEY | MIXED, TR | NW])
 def test_mix_equals_alone(alg):
     import paper_2403_16341_gb300 as nls
     payloads = I.serving_payloads(120, max_batch=1024)

@@ -26,7 +26,7 @@ def _device_group(torch, b):
     return p, u, outs
 
 
-@pytest.mark.parametrize("alg", [NEWTON | MIXED, TR, TR | MIXED, LS])
+@pytest.mark.parametrize("alg", [NEWTON | MIXED, TR, TR | MIXED, LS, TR | (1 << 13)])
 def test_noalloc_matches_handle_path_twice(alg):
     import torch
     import paper_2403_16341_gb300 as nls
