@@ -201,6 +201,9 @@ struct nls_batch {
     std::map<long long, Tuned> tuned;
     double *d_tune = nullptr; // autotuner scratch for a prefix of u
     size_t tune_bytes = 0;
+    // nls_solve_host's copy streams (created on first use) and chunk events
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    std::vector<cudaEvent_t> host_ev;
 };
 
 static std::mutex g_err_mu;
@@ -776,12 +779,12 @@ int nls_batch_create(nls_handle *out, int device, void *cuda_stream, size_t mem_
     return NLS_OK;
 }
 
-int nls_solve(nls_handle h, int family, const double *params, double *u, int n, int64_t batch, int alg,
-              double abstol, int maxiters, const nls_outputs *out, int64_t *req)
+// Enqueue one request on instances [0, batch) of arrays with leading
+// dimension ld >= batch (element e of instance k at [e * ld + k]).
+static int enqueue(nls_batch *h, int family, const double *params, double *u, int n, int64_t batch, int64_t ld,
+                   int alg, double abstol, int maxiters, const nls_outputs *out, int64_t *req)
 {
-    int rc = validate(h, family, params, u, n, batch, alg, abstol, maxiters);
-    if (rc) return rc;
-    if (!req) return fail(h, NLS_E_INVALID, "req is NULL");
+    int rc = 0;
     Request r;
     rc = select_kernel(h, family, n, alg, &r.kern, &r.tiles, &r.lanes, &r.refill, &r.rate);
     if (rc) return rc;
@@ -790,7 +793,7 @@ int nls_solve(nls_handle h, int family, const double *params, double *u, int n, 
     r.args.params = params;
     r.args.u = u;
     r.args.batch = batch;
-    r.args.ld = batch;
+    r.args.ld = ld;
     r.args.n = n;
     r.args.alg = alg & NLS_ALG_MASK;
     r.alg_flags = alg;
@@ -816,6 +819,15 @@ int nls_solve(nls_handle h, int family, const double *params, double *u, int n, 
     h->pending.push_back(r.id);
     *req = r.id;
     return NLS_OK;
+}
+
+int nls_solve(nls_handle h, int family, const double *params, double *u, int n, int64_t batch, int alg,
+              double abstol, int maxiters, const nls_outputs *out, int64_t *req)
+{
+    int rc = validate(h, family, params, u, n, batch, alg, abstol, maxiters);
+    if (rc) return rc;
+    if (!req) return fail(h, NLS_E_INVALID, "req is NULL");
+    return enqueue(h, family, params, u, n, batch, batch, alg, abstol, maxiters, out, req);
 }
 
 int nls_flush(nls_handle h)
@@ -881,22 +893,69 @@ int nls_solve_host(nls_handle h, int family, const double *params, double *u, in
     int32_t *dst = reinterpret_cast<int32_t *>(base + align(bp) + align(bu) + align((size_t)batch * 8));
     int32_t *dit = dst + align(bo) / 4;
     int32_t *dnf = dit + align(bo) / 4;
-    if (bp) NLS_CUDA(h, cudaMemcpyAsync(dp, params, bp, cudaMemcpyHostToDevice, h->stream));
-    if (bu) NLS_CUDA(h, cudaMemcpyAsync(du, u, bu, cudaMemcpyHostToDevice, h->stream));
-    nls_outputs dout{out && out->status ? dst : nullptr, out && out->iters ? dit : nullptr,
-                     out && out->resid_inf ? dres : nullptr, out && out->nfev ? dnf : nullptr};
-    int64_t req = 0;
-    rc = nls_solve(h, family, bp ? dp : nullptr, du, n, batch, alg, abstol, maxiters, &dout, &req);
-    if (rc) return rc;
-    rc = flush_pending(h);
-    if (rc) return rc;
-    if (bu) NLS_CUDA(h, cudaMemcpyAsync(u, du, bu, cudaMemcpyDeviceToHost, h->stream));
-    if (out && out->status) NLS_CUDA(h, cudaMemcpyAsync(out->status, dst, bo, cudaMemcpyDeviceToHost, h->stream));
-    if (out && out->iters) NLS_CUDA(h, cudaMemcpyAsync(out->iters, dit, bo, cudaMemcpyDeviceToHost, h->stream));
-    if (out && out->nfev) NLS_CUDA(h, cudaMemcpyAsync(out->nfev, dnf, bo, cudaMemcpyDeviceToHost, h->stream));
-    if (out && out->resid_inf)
-        NLS_CUDA(h, cudaMemcpyAsync(out->resid_inf, dres, (size_t)batch * 8, cudaMemcpyDeviceToHost, h->stream));
-    return nls_status(h, req, solved, -1);
+    // Large batches are pipelined in chunks of instances: chunk c + 1's inputs
+    // go up on s_in while chunk c is solved on the handle's stream, and the
+    // results of finished chunks come back on s_out; events order the three.
+    // Chunks address the staging arrays with leading dimension `batch`.  The
+    // poly-algorithm gathers whole arrays, so it keeps one chunk.
+    const int64_t C = ((alg & NLS_ALG_MASK) == NLS_POLYALG || batch < 4 * 65536) ? 1 : 4;
+    if (C > 1) {
+        if (!h->s_in) NLS_CUDA(h, cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking));
+        if (!h->s_out) NLS_CUDA(h, cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking));
+        while ((int64_t)h->host_ev.size() < 2 * C) {
+            cudaEvent_t e;
+            NLS_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            h->host_ev.push_back(e);
+        }
+    }
+    cudaStream_t sin = C > 1 ? h->s_in : h->stream, sout = C > 1 ? h->s_out : h->stream;
+    std::vector<int64_t> reqs;
+    for (int64_t c = 0; c < C; ++c) {
+        const int64_t k0 = batch * c / C, kc = batch * (c + 1) / C - k0;
+        if (bp)
+            NLS_CUDA(h, cudaMemcpy2DAsync(dp + k0, batch * 8, params + k0, batch * 8, kc * 8, E,
+                                          cudaMemcpyHostToDevice, sin));
+        if (bu)
+            NLS_CUDA(h, cudaMemcpy2DAsync(du + k0, batch * 8, u + k0, batch * 8, kc * 8, n, cudaMemcpyHostToDevice,
+                                          sin));
+        if (C > 1) {
+            NLS_CUDA(h, cudaEventRecord(h->host_ev[2 * c], sin));
+            NLS_CUDA(h, cudaStreamWaitEvent(h->stream, h->host_ev[2 * c], 0));
+        }
+        nls_outputs dout{out && out->status ? dst + k0 : nullptr, out && out->iters ? dit + k0 : nullptr,
+                         out && out->resid_inf ? dres + k0 : nullptr, out && out->nfev ? dnf + k0 : nullptr};
+        int64_t req = 0;
+        rc = enqueue(h, family, bp ? dp + k0 : nullptr, du + k0, n, kc, batch, alg, abstol, maxiters, &dout, &req);
+        if (rc) return rc;
+        reqs.push_back(req);
+        rc = flush_pending(h);
+        if (rc) return rc;
+        if (C > 1) {
+            NLS_CUDA(h, cudaEventRecord(h->host_ev[2 * c + 1], h->stream));
+            NLS_CUDA(h, cudaStreamWaitEvent(sout, h->host_ev[2 * c + 1], 0));
+        }
+        if (bu)
+            NLS_CUDA(h, cudaMemcpy2DAsync(u + k0, batch * 8, du + k0, batch * 8, kc * 8, n, cudaMemcpyDeviceToHost,
+                                          sout));
+        if (out && out->status)
+            NLS_CUDA(h, cudaMemcpyAsync(out->status + k0, dst + k0, kc * 4, cudaMemcpyDeviceToHost, sout));
+        if (out && out->iters)
+            NLS_CUDA(h, cudaMemcpyAsync(out->iters + k0, dit + k0, kc * 4, cudaMemcpyDeviceToHost, sout));
+        if (out && out->nfev)
+            NLS_CUDA(h, cudaMemcpyAsync(out->nfev + k0, dnf + k0, kc * 4, cudaMemcpyDeviceToHost, sout));
+        if (out && out->resid_inf)
+            NLS_CUDA(h, cudaMemcpyAsync(out->resid_inf + k0, dres + k0, kc * 8, cudaMemcpyDeviceToHost, sout));
+    }
+    NLS_CUDA(h, cudaStreamSynchronize(sout));
+    int64_t total = 0;
+    for (int64_t req : reqs) {
+        int64_t sv = 0;
+        rc = nls_status(h, req, &sv, -1);
+        if (rc) return rc;
+        total += sv;
+    }
+    if (solved) *solved = total;
+    return NLS_OK;
 }
 
 int nls_batch_destroy(nls_handle h)
@@ -913,6 +972,9 @@ int nls_batch_destroy(nls_handle h)
     if (h->d_stage) cudaFree(h->d_stage);
     if (h->d_ctr) cudaFree(h->d_ctr);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);
+    for (cudaEvent_t e : h->host_ev) cudaEventDestroy(e);
+    if (h->s_in) cudaStreamDestroy(h->s_in);
+    if (h->s_out) cudaStreamDestroy(h->s_out);
     delete h;
     return NLS_OK;
 }

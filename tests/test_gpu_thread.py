@@ -153,11 +153,19 @@ def test_api_errors(solver):
     assert e.value.code == nls.NLS_E_NOTFOUND
 
 
-def test_host_entry_point_matches_device(solver):
+@pytest.mark.parametrize("case", ["small", "chunked", "chunked_warp"])
+def test_host_entry_point_matches_device(solver, case):
+    # batches of 4 x 2^16 instances and more are pipelined in four chunks
+    # (copies on their own streams); the results equal the device-buffer path
     import ctypes
     import paper_2403_16341_gb300 as nls
-    b = I.cubic_batch(8, 2000, config_id=1, b_half_width=5.0)
-    g = gpu_solve(solver, b, TR | MIXED)
+    if case == "small":
+        b, alg = I.cubic_batch(8, 2000, config_id=1, b_half_width=5.0), TR | MIXED
+    elif case == "chunked":
+        b, alg = I.cubic_batch(8, 300001, config_id=1, b_half_width=5.0), TR | MIXED
+    else:
+        b, alg = I.bratu_batch(12, 270001, config_id=2), LS
+    g = gpu_solve(solver, b, alg)
     u = np.ascontiguousarray(b.u0.copy())
     st = np.zeros(b.batch, dtype=np.int32)
     it = np.zeros(b.batch, dtype=np.int32)
@@ -165,7 +173,7 @@ def test_host_entry_point_matches_device(solver):
     nf = np.zeros(b.batch, dtype=np.int32)
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p).value
     solved = nls.nls_solve_host(solver.h, b.family, ptr(b.params), ptr(u), b.n, b.batch,
-                                TR | MIXED, 1e-10, 50, ptr(st), ptr(it), ptr(rs), ptr(nf))
+                                alg, 1e-10, 50, ptr(st), ptr(it), ptr(rs), ptr(nf))
     assert solved == g["solved"]
     np.testing.assert_array_equal(u, g["u"])
     np.testing.assert_array_equal(st, g["status"])
