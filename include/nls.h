@@ -190,7 +190,9 @@ int nls_status(nls_handle h, int64_t req, int64_t *solved, int timeout_ms);
 /* Synchronous end-to-end variant on HOST buffers: copies params and u
  * (pinned host memory is fastest) into library-owned device memory, solves,
  * copies u and the per-instance outputs (HOST pointers in `out`, each may be
- * NULL) back, and waits.  Same arguments and errors as nls_solve, plus
+ * NULL) back, and waits.  Batches of 2^18 instances and more (not
+ * NLS_POLYALG) are pipelined in up to eight chunks: a chunk's upload, solve
+ * and download overlap the neighbouring chunks'.  Same arguments and errors as nls_solve, plus
  * NLS_E_NOMEM when the staging buffers would exceed the memory cap. */
 int nls_solve_host(nls_handle h, int family, const double *params, double *u, int n,
                    int64_t batch, int alg, double abstol, int maxiters, const nls_outputs *out,

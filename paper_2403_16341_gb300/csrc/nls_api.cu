@@ -898,7 +898,9 @@ int nls_solve_host(nls_handle h, int family, const double *params, double *u, in
     // results of finished chunks come back on s_out; events order the three.
     // Chunks address the staging arrays with leading dimension `batch`.  The
     // poly-algorithm gathers whole arrays, so it keeps one chunk.
-    const int64_t C = ((alg & NLS_ALG_MASK) == NLS_POLYALG || batch < 4 * 65536) ? 1 : 4;
+    // chunks of at least 2^17 instances (several waves of a persistent grid),
+    // at most eight: the first upload and the last download stay exposed
+    const int64_t C = (alg & NLS_ALG_MASK) == NLS_POLYALG ? 1 : std::min<int64_t>(8, std::max<int64_t>(1, batch >> 17));
     if (C > 1) {
         if (!h->s_in) NLS_CUDA(h, cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking));
         if (!h->s_out) NLS_CUDA(h, cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking));

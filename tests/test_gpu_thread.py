@@ -155,8 +155,8 @@ def test_api_errors(solver):
 
 @pytest.mark.parametrize("case", ["small", "chunked", "chunked_warp"])
 def test_host_entry_point_matches_device(solver, case):
-    # batches of 4 x 2^16 instances and more are pipelined in four chunks
-    # (copies on their own streams); the results equal the device-buffer path
+    # batches of 2^18 instances and more are pipelined in chunks of at least
+    # 2^17 (copies on their own streams); the results equal the device-buffer path
     import ctypes
     import paper_2403_16341_gb300 as nls
     if case == "small":
