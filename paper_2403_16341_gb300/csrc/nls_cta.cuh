@@ -268,15 +268,30 @@ struct CtaSolver {
                     }
                     // ... reduced over the half-warp ...
                     const unsigned hm = 0xFFFFu << (16 * (c & 1));
-                    uint64_t kmax = brow >= 0 ? best + 1 : 0; // +1: a valid zero key beats no candidate
+                    uint64_t kmax;
+                    int pmin;
+                    if constexpr (sizeof(K) == 4) {
+                        // 32-bit magnitudes: (|a| + 1, complement of the position) in
+                        // one key, so a single max gives the pivot and its position
+                        uint64_t key = brow >= 0 ? ((best + 1) << 32) | (uint32_t)~(uint32_t)bpos : 0;
 #pragma unroll
-                    for (int o = 8; o > 0; o >>= 1) {
-                        const uint64_t w = __shfl_xor_sync(hm, kmax, o);
-                        kmax = w > kmax ? w : kmax;
+                        for (int o = 8; o > 0; o >>= 1) {
+                            const uint64_t w = __shfl_xor_sync(hm, key, o);
+                            key = w > key ? w : key;
+                        }
+                        kmax = key >> 32;
+                        pmin = key ? (int)~(uint32_t)(key & 0xFFFFFFFFu) : INT_MAX;
+                    } else {
+                        kmax = brow >= 0 ? best + 1 : 0; // +1: a valid zero key beats no candidate
+#pragma unroll
+                        for (int o = 8; o > 0; o >>= 1) {
+                            const uint64_t w = __shfl_xor_sync(hm, kmax, o);
+                            kmax = w > kmax ? w : kmax;
+                        }
+                        pmin = (brow >= 0 && best + 1 == kmax) ? bpos : INT_MAX;
+#pragma unroll
+                        for (int o = 8; o > 0; o >>= 1) pmin = min(pmin, __shfl_xor_sync(hm, pmin, o));
                     }
-                    int pmin = (brow >= 0 && best + 1 == kmax) ? bpos : INT_MAX;
-#pragma unroll
-                    for (int o = 8; o > 0; o >>= 1) pmin = min(pmin, __shfl_xor_sync(hm, pmin, o));
                     const unsigned wb = __ballot_sync(hm, brow >= 0 && bpos == pmin);
                     const int src = wb ? __ffs(wb) - 1 : (16 * (c & 1));
                     const P pv = __shfl_sync(hm, bval, src);
