@@ -261,13 +261,14 @@ def extras(args, nls, solver, batch, params, u0, stream, dev):
 
 
 def run_serving(args, nls, local, alg=LS | MIXED, rate=2000.0, warm_s=1.0, meas_s=5.0,
-                pool=512) -> dict:
+                pool=512, streams=4) -> dict:
     """Open-loop serving run: Poisson arrivals at `rate` requests/s, each a
     request of the config-3 mix (1-4096 instances, n in {3, 8, 16, 32},
     cubic or Bratu), solved by the continuous-batching server.  Latency runs
     from the scheduled arrival to the results being in host memory.  A whole
     warm-up pass (its own server, other arrival times) runs first and is
-    discarded: the first pass of a process pays one-time costs."""
+    discarded: the first pass of a process pays one-time costs.  streams = 1
+    is the serial FIFO mode: one request wave at a time, in arrival order."""
     import torch
     payloads = I.serving_payloads(pool)
     pinned = []
@@ -276,16 +277,17 @@ def run_serving(args, nls, local, alg=LS | MIXED, rate=2000.0, warm_s=1.0, meas_
         u = torch.zeros(b.u0.shape, dtype=torch.float64).pin_memory()
         st = torch.zeros(b.batch, dtype=torch.int32).pin_memory()
         pinned.append((p, u, st))
-    _serve_pass(nls, local, payloads, pinned, alg, rate, 0.0, 2.0, pool, seed=1)
-    return _serve_pass(nls, local, payloads, pinned, alg, rate, warm_s, meas_s, pool, seed=0)
+    _serve_pass(nls, local, payloads, pinned, alg, rate, 0.0, 2.0, pool, 1, streams)
+    return _serve_pass(nls, local, payloads, pinned, alg, rate, warm_s, meas_s, pool, 0, streams)
 
 
-def _serve_pass(nls, local, payloads, pinned, alg, rate, warm_s, meas_s, pool, seed) -> dict:
+def _serve_pass(nls, local, payloads, pinned, alg, rate, warm_s, meas_s, pool, seed,
+                streams) -> dict:
     """One open-loop pass on a fresh server; requests arriving in the first
     warm_s seconds are not measured."""
     count = int(rate * (warm_s + meas_s))
     arrivals = I.poisson_arrivals(count, rate, seed=seed)
-    srv = nls.nls_server_create(local, 0, 4)
+    srv = nls.nls_server_create(local, 0, streams)
     tickets = [None] * count
     last_use = {}
     try:
@@ -324,7 +326,7 @@ def _serve_pass(nls, local, payloads, pinned, alg, rate, warm_s, meas_s, pool, s
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
             "sustained_solved_per_s": solved / span, "offered_instances_per_s": asked / meas_s,
             "solved_fraction": solved / asked, "max_queue": stats["max_queue"],
-            "max_inflight": stats["max_inflight"], "streams": 4,
+            "max_inflight": stats["max_inflight"], "streams": streams,
             "max_ms": float(lat.max()), "frac_over_1ms": float((lat > 1.0).mean()),
             "p99_submit_lag_ms": float(np.percentile(lag, 99)),
             "worst_at_s": float(arrivals[meas[int(lat.argmax())]])}
@@ -588,8 +590,12 @@ def run_workload(args, local):
             solver = nls.Solver(local, stream)  # fresh tuning table for the next precision
     elif args.workload == "serving":
         line["config"] = "open-loop Poisson arrivals, config-3 request mix"
-        for name, alg in (("mixed", LS | MIXED), ("fp64", LS), ("mixed_again", LS | MIXED)):
-            res[name] = run_serving(args, nls, local, alg=alg)
+        # continuous batching on four worker streams, and the serial FIFO mode
+        # (one stream: one request wave at a time) for comparison
+        for name, alg, streams in (("mixed", LS | MIXED, 4), ("fp64", LS, 4),
+                                   ("mixed_serial_fifo", LS | MIXED, 1),
+                                   ("fp64_serial_fifo", LS, 1)):
+            res[name] = run_serving(args, nls, local, alg=alg, streams=streams)
     elif args.workload == "adjoint":
         # sensitivities dL/dtheta of solved roots for random cotangents w, one
         # case per tiling: 2^20 cubic n = 8 (thread), 2^16 cubic n = 32 (warp
