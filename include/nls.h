@@ -8,9 +8,13 @@
  * (the problem statement of Sec. 2, Eq. 1, with theta = p_k), each instance
  * with Newton-Raphson (Sec. 2.1, Eq. 2), Newton-Raphson with a backtracking
  * line search (Sec. 2.2.1, Eq. 8-9) or a trust region with Powell's dogleg
- * step (Sec. 2.2.2, Eq. 12-14).  The Jacobian comes from forward-mode dual
- * numbers (Sec. 2.4) or from the family's analytic formula, and each Newton
- * system is solved with a dense LU with partial pivoting (Sec. 3.2, Fig. 5).
+ * step (Sec. 2.2.2, Eq. 12-14); or with Halley's method (Sec. 2.1, Eq. 3),
+ * the Potra-Ptak two-step method (Sec. 2.1, Eq. 4), Broyden's quasi-Newton
+ * method (Sec. 3.1, Tab. 1), or the poly-algorithm that chains them
+ * (Sec. 3.2).  The Jacobian comes from forward-mode dual numbers (Sec. 2.4)
+ * or from the family's analytic formula, and each Newton system is solved
+ * with a dense LU with partial pivoting (Sec. 3.2, Fig. 5).  nls_adjoint
+ * returns the sensitivity of the roots to the parameters (Sec. 2.3).
  * An instance has converged when ||F(u_k)||_inf <= abstol (Sec. 2.1).  The
  * paper's own GPU form of this path is Sec. 3.3: statically sized,
  * non-allocating solvers, one instance per GPU thread.
@@ -104,7 +108,7 @@ enum nls_inst_status {
     NLS_SUCCESS = 0,    /* ||F(u)||_inf <= abstol                               */
     NLS_MAXITERS = 1,   /* maxiters passes without convergence                   */
     NLS_SINGULAR = 2,   /* an LU pivot was exactly zero or not finite            */
-    NLS_NONFINITE = 3,  /* F became Inf/NaN (at u0, or after a full Newton step) */
+    NLS_NONFINITE = 3,  /* F became Inf/NaN (at u0, or after an accepted step)   */
     NLS_LS_FAILED = 4,  /* 30 backtracking trials without sufficient decrease    */
     NLS_TR_STALLED = 5, /* 32 trust-region rejections in a row                   */
     NLS_ABORTED = 6     /* the launch's deadline (NLS_OPT_DEADLINE_US) passed
