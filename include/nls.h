@@ -238,7 +238,9 @@ int nls_set_option(nls_handle h, int option, int64_t value);
  * 8, 16 or 32 lanes (n <= lanes), CTA (n > 8) -- each both as a persistent
  * grid (thread tiling: refill thresholds 0/16/24/31) and as a
  * one-block-per-chunk grid (best of three runs), on the first min(batch, 2^18) instances of this
- * batch; keeps the fastest for (family, n, algorithm, precision) in the
+ * batch; when the two fastest are within 5%, they are timed again,
+ * alternately, on the first min(batch, 2^20) instances.  Keeps the fastest
+ * for (family, n, algorithm, precision) in the
  * handle's table and restores u.  Later nls_solve calls without a tiling
  * flag use the table (a request flushed alone takes the tuned launch mode;
  * requests flushed together always use one-block-per-chunk grids).

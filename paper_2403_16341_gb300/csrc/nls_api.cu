@@ -708,7 +708,7 @@ static int load_tuning(nls_batch *h, const char *path)
 // One timed trial of a tiling on the first S instances of a request; u's
 // prefix is restored from `save` before the run.
 static int tune_trial(nls_batch *h, const SolveArgs &base, const KernelInfo &k, int refill, const double *save,
-                      int64_t S, unsigned long long *ctr, float *ms_out)
+                      int64_t save_pitch, int64_t S, unsigned long long *ctr, float *ms_out)
 {
     SolveArgs a = base;
     a.batch = S;
@@ -730,8 +730,8 @@ static int tune_trial(nls_batch *h, const SolveArgs &base, const KernelInfo &k, 
     NLS_CUDA(h, cudaEventCreate(&e1));
     float best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
-        NLS_CUDA(h, cudaMemcpy2DAsync(base.u, base.ld * 8, save, S * 8, S * 8, base.n, cudaMemcpyDeviceToDevice,
-                                      h->stream));
+        NLS_CUDA(h, cudaMemcpy2DAsync(base.u, base.ld * 8, save, save_pitch * 8, S * 8, base.n,
+                                      cudaMemcpyDeviceToDevice, h->stream));
         NLS_CUDA(h, cudaMemsetAsync(ctr, 0, 16, h->stream));
         NLS_CUDA(h, cudaEventRecord(e0, h->stream));
         cudaError_t e = k.launch(a, grid, h->stream);
@@ -1005,8 +1005,12 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
     rc = flush_pending(h);
     if (rc) return rc;
     if (batch == 0) return NLS_OK;
+    // candidates are timed on the first S instances; a close final is decided
+    // on the first SF (up to the request's size, at most 2^20), where the
+    // launch modes' tail effects are those of the real launch
     const int64_t S = std::min<int64_t>(batch, 1 << 18);
-    const size_t need = (size_t)n * (size_t)S * 8 + 256;
+    const int64_t SF = std::min<int64_t>(batch, 1 << 20);
+    const size_t need = (size_t)n * (size_t)SF * 8 + 256;
     if (need > h->tune_bytes) {
         NLS_CUDA(h, cudaStreamSynchronize(h->stream));
         if (h->d_tune) {
@@ -1019,9 +1023,9 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
         if (rc) return rc;
         h->tune_bytes = need;
     }
-    double *save = h->d_tune;
-    auto *ctr = reinterpret_cast<unsigned long long *>(h->d_tune + (size_t)n * (size_t)S);
-    NLS_CUDA(h, cudaMemcpy2DAsync(save, S * 8, u, batch * 8, S * 8, n, cudaMemcpyDeviceToDevice, h->stream));
+    double *save = h->d_tune; // the first SF instances of u, row pitch SF
+    auto *ctr = reinterpret_cast<unsigned long long *>(h->d_tune + (size_t)n * (size_t)SF);
+    NLS_CUDA(h, cudaMemcpy2DAsync(save, SF * 8, u, batch * 8, SF * 8, n, cudaMemcpyDeviceToDevice, h->stream));
     const bool mixed = (alg & NLS_MIXED) != 0, analytic = (alg & NLS_ANALYTIC_JAC) != 0;
     std::vector<Tuned> cands;
     auto add = [&](int tiles, int lanes, int refill) {
@@ -1075,14 +1079,14 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
         KernelInfo k = cand_kernel(c);
         if (!k.launch) continue;
         float ms = 0.f;
-        rc = tune_trial(h, base, k, c.refill, save, S, ctr, &ms);
+        rc = tune_trial(h, base, k, c.refill, save, SF, S, ctr, &ms);
         if (rc) return rc;
         c.rate = double(S) / (double(ms) * 1e-3);
         if (c.rate > best.rate) best = c;
     }
-    // a close final (within 5%) is decided again: the two leaders alternate
-    // for three more best-of-3 rounds, so a drift of the clock or a noisy
-    // first trial does not pick the slower launch mode
+    // a close final (within 5%) is decided again, on SF instances: the two
+    // leaders alternate for three more best-of-3 rounds, so neither a drift of
+    // the clock nor the smaller sample's tail picks the slower launch mode
     {
         std::vector<Tuned *> order;
         for (Tuned &c : cands)
@@ -1096,16 +1100,16 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
                     const Tuned &c = *fin[f];
                     KernelInfo k = cand_kernel(c);
                     float ms = 0.f;
-                    rc = tune_trial(h, base, k, c.refill, save, S, ctr, &ms);
+                    rc = tune_trial(h, base, k, c.refill, save, SF, SF, ctr, &ms);
                     if (rc) return rc;
                     bestms[f] = std::min(bestms[f], ms);
                 }
             }
-            for (int f = 0; f < 2; ++f) fin[f]->rate = double(S) / (double(bestms[f]) * 1e-3);
+            for (int f = 0; f < 2; ++f) fin[f]->rate = double(SF) / (double(bestms[f]) * 1e-3);
             best = fin[0]->rate >= fin[1]->rate ? *fin[0] : *fin[1];
         }
     }
-    NLS_CUDA(h, cudaMemcpy2DAsync(u, batch * 8, save, S * 8, S * 8, n, cudaMemcpyDeviceToDevice, h->stream));
+    NLS_CUDA(h, cudaMemcpy2DAsync(u, batch * 8, save, SF * 8, SF * 8, n, cudaMemcpyDeviceToDevice, h->stream));
     NLS_CUDA(h, cudaStreamSynchronize(h->stream));
     h->tuned[tune_key(family, n, alg)] = best;
     if (chosen) *chosen = best.tiles;
