@@ -1,0 +1,58 @@
+"""Host-side bookkeeping of the benchmark line (no GPU): the algorithmic FP64
+flop count behind the roofline's `achieved`, and the tie between the stored
+DRAM traffic and the kernel sources it was measured on."""
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_flops_per_residual_and_pass(bench):
+    n = 8
+    iters = np.array([5])
+    nfev = np.array([6])
+    # residual of the cubic: n^2 products and n^2 sums for A u (2n^2), the
+    # cube and the - b (3n); squared norm 2n; trial point 2n -> 128 + 24 + 32
+    res = 184
+    # LU 2n^3/3 - n^2/2 - n/6 = 341.33 - 32 - 1.33 = 308; solves 2n^2 = 128;
+    # analytic-equivalent Jacobian 2n = 16
+    per_pass = 308 + 128 + 16
+    LS, TR, MIXED = 1, 2, 1 << 8
+    assert bench.algorithmic_fp64_flops(n, LS, iters, nfev) == pytest.approx(6 * res + 5 * per_pass)
+    # the dogleg adds 10n of scalar work per pass
+    assert bench.algorithmic_fp64_flops(n, TR, iters, nfev) == pytest.approx(6 * res + 5 * (per_pass + 80))
+    # mixed mode: the Jacobian and LU are FP32, only the residual side counts
+    assert bench.algorithmic_fp64_flops(n, TR | MIXED, iters, nfev) == pytest.approx(6 * res)
+
+
+def test_traffic_is_tied_to_the_kernel_sources(bench, monkeypatch):
+    h = bench.thread_kernel_hash()
+    path = os.path.join(ROOT, "profiles", "counters_thread_cubic_n8.txt")
+    rows = {}
+    for line in open(path):
+        parts = line.split()
+        if len(parts) == 3 and not line.startswith("#"):
+            rows[parts[0]] = (int(parts[1]), parts[2])
+    assert set(rows) == {"newton_backtrack_fp64", "newton_backtrack_mixed", "trust_dogleg_fp64",
+                         "trust_dogleg_mixed"}
+    for variant, (nbytes, digest) in rows.items():
+        # algorithmic bytes of a 2^20 launch: 724 B per instance; the capture
+        # is at or below it (part of the output still sits in L2 at the end)
+        assert 0.9 * 724 * 2 ** 20 < nbytes <= 724 * 2 ** 20
+        expected = nbytes if digest == h else None
+        assert bench.dram_traffic(variant) == expected
+    # any change of the sources voids the stored counters
+    monkeypatch.setattr(bench, "THREAD_KERNEL_SOURCES", bench.THREAD_KERNEL_SOURCES[:-1])
+    assert bench.thread_kernel_hash() != h
+    assert all(bench.dram_traffic(v) is None for v in rows)
