@@ -74,7 +74,10 @@ cudaError_t launch_poly_gather(const PolyGatherArgs &g, cudaStream_t st);
 cudaError_t launch_poly_scatter(const PolyScatterArgs &s, cudaStream_t st);
 cudaError_t launch_poly_total(unsigned long long *solved, const unsigned long long *ctr, int stages,
                               cudaStream_t st);
-// stage kernels of the poly-algorithm's quasi-Newton phase
+// Potra-Ptak, Halley, Broyden and modified Broyden (alg = ALG_POTRA_PTAK ..
+// ALG_MOD_BROYDEN): one instance per thread (n <= 8), per warp segment of
+// L = 16 or 32 lanes, or per CTA (n <= 128).
+KernelInfo thread_ext_kernel(int family, int n, int alg, bool mixed);
 KernelInfo warp_ext_kernel(int family, int L, int alg, bool mixed);
 KernelInfo cta_ext_kernel(int family, int n, int alg, bool mixed);
 } // namespace nls
