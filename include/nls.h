@@ -8,7 +8,7 @@
  * (the problem statement of Sec. 2, Eq. 1, with theta = p_k), each instance
  * with Newton-Raphson (Sec. 2.1, Eq. 2), Newton-Raphson with a backtracking
  * line search (Sec. 2.2.1, Eq. 8-9) or a trust region with Powell's dogleg
- * step (Sec. 2.2.2, Eq. 12-14); or with Halley's method (Sec. 2.1, Eq. 3),
+ * step (Sec. 2.2.2, Eq. 13-15); or with Halley's method (Sec. 2.1, Eq. 3),
  * the Potra-Ptak two-step method (Sec. 2.1, Eq. 4), Broyden's quasi-Newton
  * method (Sec. 3.1, Tab. 1), or the poly-algorithm that chains them
  * (Sec. 3.2).  The Jacobian comes from forward-mode dual numbers (Sec. 2.4)
@@ -57,7 +57,7 @@ enum nls_family { NLS_CUBIC = 0, NLS_BRATU = 1, NLS_SQUARE = 2, NLS_ROSENBROCK =
 enum nls_alg {
     NLS_NEWTON = 0,           /* Sec. 2.1, Eq. 2                               */
     NLS_NEWTON_BACKTRACK = 1, /* Sec. 2.2.1: Armijo (Eq. 8-9), alpha <- alpha/2 */
-    NLS_TRUST_DOGLEG = 2,     /* Sec. 2.2.2: Eq. 12-14, Powell's dogleg          */
+    NLS_TRUST_DOGLEG = 2,     /* Sec. 2.2.2: Eq. 13-15, Powell's dogleg          */
     NLS_POLYALG = 3,          /* Sec. 3.2 poly-algorithm: the first stage runs
                                  on every instance, the ones that fail
                                  restart from u0 with the next stage.  n > 25:

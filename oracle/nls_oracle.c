@@ -16,7 +16,7 @@
  *   Sec. 2.1, Eq. 2      Newton-Raphson: J_k du = -f(u_k), u_{k+1} = u_k + du
  *   Sec. 2.2.1, Eq. 8-9  Armijo sufficient decrease on phi = 1/2 ||f||^2,
  *                        slope f^T J du; backtracking: alpha_0 = 1, alpha <- rho alpha
- *   Sec. 2.2.2, Eq. 12-14 trust-region model, ratio rho_k, radius update,
+ *   Sec. 2.2.2, Eq. 13-15 trust-region model, ratio rho_k, radius update,
  *                        Powell's dogleg
  *   Sec. 3.2 (Fig. 5)    small dense systems use a native LU (partial pivoting)
  *   Sec. 2.2.1, Eq. 5    generalized Rosenbrock function
@@ -502,7 +502,7 @@ static void solve_one(int family, int n, const double *p, double *u, int alg, do
             nfev++;
             if (tr) { tr->alpha[k - 1] = 1.0; tr->trials[k - 1] = 1; }
         } else {
-            /* trust region with the dogleg step (Eq. 12-14) */
+            /* trust region with the dogleg step (Eq. 13-15) */
             double fF, ared, pred, rho;
             int branch = oracle_dogleg(n, J, F, dN, Delta, d);
             for (i = 0; i < n; i++)

@@ -72,7 +72,7 @@ struct SolveArgs {
     int tr_scheme; // TR_SIMPLE or TR_NOCEDAL_WRIGHT
 };
 
-// Outcome of one trust-region trial step (Sec. 2.2.2, Eq. 14): returns
+// Outcome of one trust-region trial step (Sec. 2.2.2, Eq. 15): returns
 // whether the step is accepted and updates the radius.  ok: pred > 0 and
 // F(u + d) finite (otherwise rho = -inf); boundary: the dogleg step ended on
 // the region's boundary (branch C or D).  With pred > 0 every comparison of

@@ -598,7 +598,7 @@ struct CtaSolver {
                 aa = P(r2[0]);
                 bb = P(r2[1]);
             }
-            // pred = -2 F.Jd - ||Jd||^2 (Eq. 14) from block-uniform scalars:
+            // pred = -2 F.Jd - ||Jd||^2 (Eq. 15) from block-uniform scalars:
             // J dN = -F and F.(J g) = g.g (g = J^T F), so no J d is formed
             double d, pred;
             if (nN2 <= D2) {

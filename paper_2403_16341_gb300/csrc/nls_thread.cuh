@@ -10,7 +10,7 @@
 // Jacobian by forward-mode duals (Sec. 2.4) or the analytic formula, LU with
 // partial pivoting (Sec. 3.2), then the step of the chosen globalisation:
 // full step, backtracking on the Armijo condition (Sec. 2.2.1, Eq. 8-9), or
-// the dogleg trust-region step with the ratio test (Sec. 2.2.2, Eq. 12-14).
+// the dogleg trust-region step with the ratio test (Sec. 2.2.2, Eq. 13-15).
 // Convergence is ||F||_inf <= abstol (Sec. 2.1).
 //
 // Scheduling: all lanes of a warp execute the same pass in lock step (a
@@ -329,7 +329,7 @@ struct ThreadSolver {
             need_jac = true;
         } else {
             // Powell's dogleg on m(d) = 1/2||F||^2 + d^T J^T F + 1/2 d^T J^T J d, ||d||_2 <= Delta.
-            // pred = ||F||^2 - ||F + J d||^2 = -2 F.Jd - ||Jd||^2 (Eq. 14) by linearity:
+            // pred = ||F||^2 - ||F + J d||^2 = -2 F.Jd - ||Jd||^2 (Eq. 15) by linearity:
             // J dN = -F and, with g = J^T F, F.(J g) = g.g, so every branch's pred is
             // a combination of ||F||^2, ||g||^2 and ||J g||^2 (no vector J d is formed).
             double d[N];
@@ -384,7 +384,7 @@ struct ThreadSolver {
             residual(pv, ut, Ft);
             ++nfev;
             const double fFt = sumsq(Ft);
-            // rho = ared / pred (Eq. 14)
+            // rho = ared / pred (Eq. 15)
             const double ared = fF - fFt;
             const bool ok = pred > 0.0 && max_mag_bits(Ft) < INF64_BITS;
             if (tr_step_outcome(a.tr_scheme, ok, ared, pred, boundary, Delta)) {

@@ -16,7 +16,7 @@
 // All segments of a warp execute each pass in lock step (idle segments run
 // masked); a persistent launch refills idle segments from a work counter.
 // The globalisations are those of the thread tiling: Newton (Eq. 2),
-// backtracking on Eq. 8-9, dogleg trust region with Eq. 14.
+// backtracking on Eq. 8-9, dogleg trust region with Eq. 13-15.
 #pragma once
 
 #include "nls_common.cuh"
@@ -396,7 +396,7 @@ struct WarpSolver {
             const P w = P(dN) + t * g; // dN - c
             const P aa = seg_sum<L>(w * w, 0xffffffffu);
             const P bb = seg_sum<L>(-t * g * w, 0xffffffffu);
-            // pred = -2 F.Jd - ||Jd||^2 (Eq. 14) from segment-uniform scalars:
+            // pred = -2 F.Jd - ||Jd||^2 (Eq. 15) from segment-uniform scalars:
             // J dN = -F and F.(J g) = g.g (g = J^T F), so no J d is formed
             double d, pred;
             if (nN2 <= D2) {
