@@ -451,7 +451,8 @@ def test_adjoint_square_example_sec2_3():
         assert grad[1 - i] == 0.0
 
 
-@pytest.mark.parametrize("family,n", [(CUBIC, 3), (CUBIC, 6), (BRATU, 5), (SQUARE, 4)])
+@pytest.mark.parametrize("family,n", [(CUBIC, 3), (CUBIC, 6), (BRATU, 5), (SQUARE, 4),
+                                      (CUBIC, 20), (BRATU, 64), (SQUARE, 40)])
 def test_adjoint_matches_finite_differences(family, n):
     rng = np.random.default_rng(7)
     if family == CUBIC:
@@ -466,7 +467,9 @@ def test_adjoint_matches_finite_differences(family, n):
     grad, sing = O.adjoint(family, p, u, w)
     assert not sing
     for e in range(p.size):
-        h = 1e-6 * max(1.0, abs(p[e]))
+        # larger systems reach their root to about n eps cond(J): a wider
+        # difference step keeps that round-off below the tolerance
+        h = (1e-6 if n <= 8 else 1e-4) * max(1.0, abs(p[e]))
         pp, pm = p.copy(), p.copy()
         pp[e] += h
         pm[e] -= h
