@@ -211,7 +211,20 @@ struct ThreadSolver {
 
     // ------------------------------------------------------------ lane state
     double u[N], F[N], dN[N];
-    P g[N], Jg[N], Fp[N], dNp[N]; // dNp: the Newton step in the Jacobian precision
+    P g[N], Jg[N];
+    // F and the Newton step in the Jacobian precision; in FP64 mode they are
+    // F and dN themselves (no second copy across passes)
+    P Fp_[MIXED ? N : 1], dNp_[MIXED ? N : 1];
+    NLS_DI P Fp(int i) const
+    {
+        if constexpr (MIXED) return Fp_[i];
+        else return F[i];
+    }
+    NLS_DI P dNp(int i) const
+    {
+        if constexpr (MIXED) return dNp_[i];
+        else return dN[i];
+    }
     double fF, Delta;
     int it, nfev, rej, status;
     bool need_jac;
@@ -253,7 +266,7 @@ struct ThreadSolver {
         for (int j = 0; j < N; ++j) {
             P s = P(0);
 #pragma unroll
-            for (int i = 0; i < N; ++i) s = fma(J[i][j], Fp[i], s);
+            for (int i = 0; i < N; ++i) s = fma(J[i][j], Fp(i), s);
             g[j] = s;
         }
         if (jg) {
@@ -275,19 +288,20 @@ struct ThreadSolver {
             P J[N][N], b[N];
             jacobian(pv, u, J);
 #pragma unroll
-            for (int i = 0; i < N; ++i) Fp[i] = P(F[i]);
+            for (int i = 0; i < N; ++i)
+                if constexpr (MIXED) Fp_[i] = P(F[i]);
             // the trust region forms g = J^T F and J g only when the Newton step
             // leaves the region (J is re-evaluated then: the LU overwrites it)
             have_g = false;
 #pragma unroll
-            for (int i = 0; i < N; ++i) b[i] = -Fp[i];
+            for (int i = 0; i < N; ++i) b[i] = -Fp(i);
             if (!lu_solve<N, P>(J, b)) {
                 status = ST_SINGULAR;
                 return;
             }
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-                dNp[i] = b[i];
+                if constexpr (MIXED) dNp_[i] = b[i];
                 dN[i] = double(b[i]);
             }
             need_jac = false;
@@ -337,7 +351,7 @@ struct ThreadSolver {
             const P D2 = P(Delta * Delta);
             P nN2 = P(0);
 #pragma unroll
-            for (int i = 0; i < N; ++i) nN2 = fma(dNp[i], dNp[i], nN2);
+            for (int i = 0; i < N; ++i) nN2 = fma(dNp(i), dNp(i), nN2);
             const bool boundary = !(nN2 <= D2);
             if (nN2 <= D2) {
 #pragma unroll
@@ -365,7 +379,7 @@ struct ThreadSolver {
                     P w[N], aa = P(0), bb = P(0);
 #pragma unroll
                     for (int i = 0; i < N; ++i) {
-                        w[i] = dNp[i] + t * g[i];
+                        w[i] = dNp(i) + t * g[i];
                         aa = fma(w[i], w[i], aa);
                         bb = fma(-t * g[i], w[i], bb);
                     }
