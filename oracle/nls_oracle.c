@@ -51,6 +51,7 @@
  * contraction, so every operation is one IEEE double rounding).
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -371,8 +372,36 @@ typedef struct {
     int *trials;
 } oracle_trace;
 
+/* Test-only perturbation of the steps ("jitter"), off unless a caller asks
+ * for it: every component of every linear-solve result is multiplied by
+ * 1 + eps or 1 - eps, the sign drawn from a SplitMix64 stream (Steele, Lea
+ * & Flood 2014) keyed by (seed, instance) and advanced once per component.
+ * The parity tests use it to find the instances whose outcome changes under
+ * perturbations of the size of the rounding of another correct solver
+ * (another operation order, FMA; FP32 for mixed precision). */
+typedef struct {
+    double eps;
+    uint64_t state;
+} oracle_jitter;
+
+static uint64_t splitmix64_next(uint64_t *state)
+{
+    uint64_t z = (*state += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+static void jitter_step(oracle_jitter *jt, int n, double *x)
+{
+    int i;
+    if (!jt || jt->eps == 0.0) return;
+    for (i = 0; i < n; i++)
+        x[i] *= (splitmix64_next(&jt->state) >> 63) ? 1.0 + jt->eps : 1.0 - jt->eps;
+}
+
 static void solve_one(int family, int n, const double *p, double *u, int alg, double abstol,
-                      int maxiters, oracle_result *res, const oracle_trace *tr)
+                      int maxiters, oracle_result *res, const oracle_trace *tr, oracle_jitter *jt)
 {
     size_t nn = (size_t)n * (size_t)n;
     double *J = malloc(sizeof(double) * (3 * nn + 9 * (size_t)n));
@@ -417,6 +446,7 @@ static void solve_one(int family, int n, const double *p, double *u, int alg, do
             for (i = 0; i < n; i++)
                 rhs[i] = -F[i];
             oracle_lu_solve(n, LU, piv, rhs, d);
+            jitter_step(jt, n, d);
             for (i = 0; i < n; i++)
                 ut[i] = u[i] + d[i];
             oracle_residual(family, n, p, ut, Ft);
@@ -438,6 +468,7 @@ static void solve_one(int family, int n, const double *p, double *u, int alg, do
             for (i = 0; i < n; i++)
                 rhs[i] = -F[i];
             oracle_lu_solve(n, LU, piv, rhs, dN);
+            jitter_step(jt, n, dN);
         }
         if (alg == ALG_BROYDEN || alg == ALG_MOD_BROYDEN) {
             /* step taken above */
@@ -483,6 +514,7 @@ static void solve_one(int family, int n, const double *p, double *u, int alg, do
             for (i = 0; i < n; i++)
                 rhs[i] = -Ft[i];
             oracle_lu_solve(n, LU, piv, rhs, d);
+            jitter_step(jt, n, d);
             for (i = 0; i < n; i++)
                 u[i] = ut[i] + d[i];
             oracle_residual(family, n, p, u, F);
@@ -492,6 +524,7 @@ static void solve_one(int family, int n, const double *p, double *u, int alg, do
             /* Eq. 3: a = dN, J_k b = H_k a a, du = (a o a) / (a + b/2) */
             oracle_hvv(family, n, p, u, dN, h);
             oracle_lu_solve(n, LU, piv, h, bv);
+            jitter_step(jt, n, bv);
             for (i = 0; i < n; i++) {
                 double den = dN[i] + 0.5 * bv[i];
                 d[i] = (den != 0.0) ? (dN[i] * dN[i]) / den : dN[i];
@@ -588,12 +621,16 @@ int oracle_solve_trace(int family, int n, const double *p, double *u, int alg, d
 {
     oracle_result r;
     oracle_trace t = {alpha, branch, rho, radius, fnorm, trials};
-    solve_one(family, n, p, u, alg, abstol, maxiters, &r, &t);
+    solve_one(family, n, p, u, alg, abstol, maxiters, &r, &t, 0);
     *iters = r.iters;
     *resid = r.resid;
     *nfev = r.nfev;
     return r.status;
 }
+
+void oracle_solve_range_jitter(int family, int n, long k0, long k1, const double *params,
+                               double *u, int alg, double abstol, int maxiters, int *status,
+                               int *iters, double *resid, int *nfev, double eps, uint64_t seed);
 
 /* Solve instances [k0, k1) of a batch stored instance-major:
  * params[k*E + e] (E = oracle_n_params) and u[k*n + i] (in/out). */
@@ -601,12 +638,27 @@ void oracle_solve_range(int family, int n, long k0, long k1, const double *param
                         int alg, double abstol, int maxiters, int *status, int *iters,
                         double *resid, int *nfev)
 {
+    oracle_solve_range_jitter(family, n, k0, k1, params, u, alg, abstol, maxiters, status, iters,
+                              resid, nfev, 0.0, 0);
+}
+
+/* As oracle_solve_range, with the steps of instance k perturbed by the
+ * relative size eps (test infrastructure, see oracle_jitter); the sign
+ * stream of instance k depends on (seed, k) only. */
+void oracle_solve_range_jitter(int family, int n, long k0, long k1, const double *params,
+                               double *u, int alg, double abstol, int maxiters, int *status,
+                               int *iters, double *resid, int *nfev, double eps, uint64_t seed)
+{
     long k;
     int E = oracle_n_params(family, n);
     for (k = k0; k < k1; k++) {
         oracle_result r;
+        oracle_jitter jt;
+        uint64_t key = seed;
+        jt.eps = eps;
+        jt.state = splitmix64_next(&key) ^ (uint64_t)k;
         solve_one(family, n, params + (size_t)k * (size_t)E, u + (size_t)k * (size_t)n, alg,
-                  abstol, maxiters, &r, 0);
+                  abstol, maxiters, &r, 0, &jt);
         status[k] = r.status;
         iters[k] = r.iters;
         resid[k] = r.resid;

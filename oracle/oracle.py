@@ -63,6 +63,9 @@ def _load():
             lib.oracle_solve_range.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_long,
                                                ctypes.c_long, _D, _D, ctypes.c_int,
                                                ctypes.c_double, ctypes.c_int, _I, _I, _D, _I]
+            lib.oracle_solve_range_jitter.argtypes = [
+                ctypes.c_int, ctypes.c_int, ctypes.c_long, ctypes.c_long, _D, _D, ctypes.c_int,
+                ctypes.c_double, ctypes.c_int, _I, _I, _D, _I, ctypes.c_double, ctypes.c_uint64]
             lib.oracle_polish.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_int]
             lib.oracle_polish.restype = ctypes.c_double
             lib.oracle_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
@@ -172,15 +175,18 @@ def solve_trace(family: int, p, u0, alg: int, abstol: float = 1e-10, maxiters: i
 
 
 def solve_batch(family: int, params, u0, alg: int, abstol: float = 1e-10, maxiters: int = 50,
-                threads: int = 1):
+                threads: int = 1, jitter: float = 0.0, seed: int = 0):
     """Solve a batch given element-major params[E, B], u0[n, B].
+
+    jitter > 0 (tests only) multiplies every component of every computed
+    step by 1 +- jitter, signs from a stream keyed by (seed, instance).
 
     Returns (u[n, B], status[B], iters[B], resid[B], nfev[B])."""
     u0 = np.asarray(u0, dtype=np.float64)
     n, B = u0.shape
     params = np.asarray(params, dtype=np.float64).reshape(-1, B)
     P = np.ascontiguousarray(params.T) if params.shape[0] else np.zeros((B, 1))
-    U = np.ascontiguousarray(u0.T)
+    U = np.array(u0.T, order="C", copy=True)  # always a copy: the C code writes the roots here
     status = np.zeros(B, dtype=np.int32)
     iters = np.zeros(B, dtype=np.int32)
     nfev = np.zeros(B, dtype=np.int32)
@@ -190,8 +196,13 @@ def solve_batch(family: int, params, u0, alg: int, abstol: float = 1e-10, maxite
         P = np.zeros((1, 1))  # no parameters: every instance gets the same unread vector
 
     def run(k0: int, k1: int) -> None:
-        lib.oracle_solve_range(family, n, k0, k1, _dp(P), _dp(U), alg, float(abstol),
-                               int(maxiters), _ip(status), _ip(iters), _dp(resid), _ip(nfev))
+        if jitter:
+            lib.oracle_solve_range_jitter(family, n, k0, k1, _dp(P), _dp(U), alg, float(abstol),
+                                          int(maxiters), _ip(status), _ip(iters), _dp(resid),
+                                          _ip(nfev), float(jitter), int(seed))
+        else:
+            lib.oracle_solve_range(family, n, k0, k1, _dp(P), _dp(U), alg, float(abstol),
+                                   int(maxiters), _ip(status), _ip(iters), _dp(resid), _ip(nfev))
 
     if threads <= 1 or B < 2 * threads:
         run(0, B)
