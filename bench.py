@@ -48,25 +48,31 @@ VARIANTS = [("newton_backtrack_fp64", LS), ("newton_backtrack_mixed", LS | MIXED
 WORKLOAD = "cubic n=8, 2^20 instances, NR+backtracking and TR-dogleg x {FP64, mixed}"
 METRIC = "solved systems/s at ||F||inf<=1e-10 (FP64 vs mixed, 1 GB300)"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x DFMA/clk x flop/FMA x max clock
+FP64_PROBED_TFLOPS = 1.19  # this repository's FP64 FMA-loop probe on a GB300 at 2.07 GHz
 
 
-def algorithmic_fp64_flops(n: int, alg: int, iters: np.ndarray, nfev: np.ndarray) -> float:
+def algorithmic_fp64_flops(n: int, alg: int, iters: np.ndarray, nfev: np.ndarray,
+                           ngrad: np.ndarray | None = None) -> float:
     """Useful FP64 flops of one solve batch (dual-number and padding overheads
     are implementation cost and not counted).  Per residual evaluation of the
     cubic: 2n^2 + 3n, plus 2n for the squared norm and 2n for forming the
     trial point.  In FP64 mode every pass also factors and solves:
     LU 2n^3/3 - n^2/2 - n/6, triangular solves 2n^2, analytic-equivalent
     Jacobian 2n, and 10n for the dogleg's scalar work (trust region).  The
-    line search's slope F^T J dN is -||F||^2 by linearity and the trust
-    region forms J^T F and J g only when the Newton step leaves the region,
-    so neither matrix-vector product is counted.  Mixed mode runs the
-    Jacobian and the LU in FP32, so only the residual-side terms are FP64."""
+    trust region forms g = J^T F and J g (2n^2 each) on the passes the kernel
+    counts in ngrad (those whose Newton step leaves the region).  Products
+    that linearity makes unnecessary are not counted: the line search's slope
+    F^T J dN = -||F||^2 and the model's J d (J dN = -F, F.(J g) = g.g).  Mixed
+    mode runs the Jacobian, the LU and the model products in FP32, so only
+    the residual-side terms are FP64."""
     res = (2 * n * n + 3 * n) + 2 * n + 2 * n
     f = float(nfev.sum()) * res
     if not alg & MIXED:
         per_pass = (2 * n ** 3 / 3 - n * n / 2 - n / 6) + 2 * n * n + 2 * n
         per_pass += 0 if (alg & 0xFF) == LS else 10 * n
         f += float(iters.sum()) * per_pass
+        if (alg & 0xFF) == TR and ngrad is not None:
+            f += float(ngrad.sum()) * 4 * n * n
     return f
 
 
@@ -260,7 +266,7 @@ def extras(args, nls, solver, batch, params, u0, stream, dev):
     return baseline, e2e
 
 
-def run_serving(args, nls, local, alg=LS | MIXED, rate=2000.0, warm_s=1.0, meas_s=5.0,
+def run_serving(args, nls, local, alg=LS | MIXED, rate=2000.0, warm_s=1.0, meas_s=10.0,
                 pool=512, streams=4) -> dict:
     """Open-loop serving run: Poisson arrivals at `rate` requests/s, each a
     request of the config-3 mix (1-4096 instances, n in {3, 8, 16, 32},
@@ -285,18 +291,21 @@ def _serve_pass(nls, local, payloads, pinned, alg, rate, warm_s, meas_s, pool, s
                 streams) -> dict:
     """One open-loop pass on a fresh server; requests arriving in the first
     warm_s seconds are not measured."""
+    import gc
     count = int(rate * (warm_s + meas_s))
     arrivals = I.poisson_arrivals(count, rate, seed=seed)
     srv = nls.nls_server_create(local, 0, streams)
     tickets = [None] * count
     last_use = {}
+    gc.collect()
+    gc.disable()  # a collection in the client's submit loop delays arrivals by milliseconds
     try:
         t0 = nls.nls_server_now(srv) + 0.05
         for i in range(count):
             j = i % pool
             if j in last_use:  # the payload's buffers are free again once its last use is done
                 prev = last_use.pop(j)
-                tickets[prev] = (tickets[prev][0], nls.nls_server_wait(srv, tickets[prev][0]))
+                tickets[prev] = (tickets[prev][0], nls.nls_server_wait_timed(srv, tickets[prev][0]))
             b = payloads[j]
             p, u, st = pinned[j]
             u.zero_()
@@ -310,26 +319,54 @@ def _serve_pass(nls, local, payloads, pinned, alg, rate, warm_s, meas_s, pool, s
             last_use[j] = i
         for i in range(count):
             if tickets[i][1] is None:
-                tickets[i] = (tickets[i][0], nls.nls_server_wait(srv, tickets[i][0]))
+                tickets[i] = (tickets[i][0], nls.nls_server_wait_timed(srv, tickets[i][0]))
         stats = nls.nls_server_stats(srv)
     finally:
+        gc.enable()
         nls.nls_server_destroy(srv)
     meas = [i for i in range(count) if arrivals[i] >= warm_s]
-    lat = np.array([tickets[i][1][2] - (t0 + arrivals[i]) for i in meas]) * 1e3
-    lag = np.array([tickets[i][1][1] - (t0 + arrivals[i]) for i in meas]) * 1e3  # submit delay
+    tm = [tickets[i][1][1] for i in meas]
+    lat = np.array([t["t_done"] - (t0 + arrivals[i]) for t, i in zip(tm, meas)]) * 1e3
+    lag = np.array([t["t_submit"] - (t0 + arrivals[i]) for t, i in zip(tm, meas)]) * 1e3
     solved = sum(tickets[i][1][0] for i in meas)
     asked = sum(payloads[i % pool].batch for i in meas)
-    span = max(tickets[i][1][2] for i in meas) - (t0 + arrivals[meas[0]])
+    span = max(t["t_done"] for t in tm) - (t0 + arrivals[meas[0]])
+    # where the time went: arrival -> submit (client), submit -> admit (queue),
+    # admit -> launch (copies and solve enqueued), then on the device the
+    # wave's input copies, its solve and the copy back; what is left of
+    # launch -> done is waiting behind earlier work on the stream plus the
+    # dispatcher noticing completion
+    stages = {
+        "submit_lag": lag,
+        "queue": np.array([t["t_admit"] - t["t_submit"] for t in tm]) * 1e3,
+        "enqueue": np.array([t["t_launch"] - t["t_admit"] for t in tm]) * 1e3,
+        "h2d": np.array([t["h2d_ms"] for t in tm]),
+        "solve": np.array([t["solve_ms"] for t in tm]),
+        "d2h": np.array([t["d2h_ms"] for t in tm]),
+    }
+    dev = stages["h2d"] + stages["solve"] + stages["d2h"]
+    server = np.array([t["t_done"] - t["t_submit"] for t in tm]) * 1e3  # the server's own part
+    stages["stream_wait_and_notice"] = np.array([t["t_done"] - t["t_launch"] for t in tm]) * 1e3 - dev
+    worst = int(lat.argmax())
+    wreq = payloads[meas[worst] % pool]
+    breakdown = {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99)),
+                     "max": float(v.max())} for k, v in stages.items()}
     return {"workload": "Poisson arrivals at 2000 req/s, 1-4096 instances per request "
                         "(log-uniform), n in {3,8,16,32}, cubic or Bratu, NR+backtracking mixed",
             "requests": len(meas), "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "server_p50_ms": float(np.percentile(server, 50)),
+            "server_p99_ms": float(np.percentile(server, 99)), "server_max_ms": float(server.max()),
             "sustained_solved_per_s": solved / span, "offered_instances_per_s": asked / meas_s,
             "solved_fraction": solved / asked, "max_queue": stats["max_queue"],
             "max_inflight": stats["max_inflight"], "streams": streams,
             "max_ms": float(lat.max()), "frac_over_1ms": float((lat > 1.0).mean()),
             "p99_submit_lag_ms": float(np.percentile(lag, 99)),
-            "worst_at_s": float(arrivals[meas[int(lat.argmax())]])}
+            "worst_at_s": float(arrivals[meas[worst]]),
+            "stages_ms": breakdown,
+            "worst_request": {"latency_ms": float(lat[worst]), "n": wreq.n, "batch": wreq.batch,
+                              "family": wreq.family, "wave_requests": tm[worst]["wave_requests"],
+                              **{k: float(v[worst]) for k, v in stages.items()}}}
 
 
 def run_ours(args, world, rank, local):
@@ -354,7 +391,8 @@ def run_ours(args, world, rank, local):
     us = [torch.empty_like(u0) for _ in VARIANTS]
     B = batch.batch
     outs = [tuple(torch.empty(B, dtype=dt, device=dev) for dt in
-                  (torch.int32, torch.int32, torch.float64, torch.int32)) for _ in VARIANTS]
+                  (torch.int32, torch.int32, torch.float64, torch.int32, torch.int32))
+            for _ in VARIANTS]
     def new_events():
         return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                 for _ in VARIANTS]
@@ -420,13 +458,14 @@ def run_ours(args, world, rank, local):
     variants = {}
     dom, dom_ms = None, -1.0
     for i, (name, alg) in enumerate(VARIANTS):
-        st, it, rs, nf = (t.cpu().numpy() for t in outs[i])
+        st, it, rs, nf, ng = (t.cpu().numpy() for t in outs[i])
         ms = float(np.median(per_variant[i]))
-        fl = algorithmic_fp64_flops(N_SYS, alg, it, nf)
+        fl = algorithmic_fp64_flops(N_SYS, alg, it, nf, ng)
         solved = int((st == 0).sum())
         variants[name] = {"ms": ms, "solved_per_s": solved / (ms / 1e3), "solved": solved,
                           "tiling": chosen.get(name, "default"),
                           "mean_iters": float(it.mean()), "max_iters": int(it.max()),
+                          "mean_nfev": float(nf.mean()), "mean_gradient_passes": float(ng.mean()),
                           "fp64_gflop": fl / 1e9, "fp64_tflops": fl / (ms / 1e3) / 1e12,
                           "max_resid": float(rs.max())}
         if ms > dom_ms:
@@ -440,6 +479,15 @@ def run_ours(args, world, rank, local):
     serving = None
     if not args.no_extras and not args.no_serving:
         serving = run_serving(args, nls, local)
+
+    # the other configurations of the benchmark, each with its own clock record
+    configs = None
+    if not args.no_extras and not args.no_configs and world == 1:
+        configs = {
+            "config0_cubic_n3": config0_cubic3(torch, solver, dev, stream, 4000, 3),
+            "config2_uneven": config2_uneven(torch, nls, local, dev, stream, 10, 3, modes=True),
+            "config4_bratu_large": config4_bratu_large(torch, solver, dev, stream, 5, 3),
+        }
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -471,8 +519,10 @@ def run_ours(args, world, rank, local):
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                         "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
-            "serving": serving,
+                         "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                         "peak_probed": FP64_PROBED_TFLOPS,
+                         "frac_of_probed": achieved / FP64_PROBED_TFLOPS},
+            "serving": serving, "configs": configs,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),
         }
@@ -499,7 +549,9 @@ def _device_batches(torch, batches, dev):
 
 def time_flush(torch, solver, dbs, alg, steps, warmup, stream):
     """Solve every batch of `dbs` in one flush, `steps` times after `warmup`;
-    returns (median ms per flush, solved per flush, launches per flush)."""
+    `alg` is one algorithm word or one per batch.  Returns (median ms per
+    flush, solved per flush, launches per flush)."""
+    algs = list(alg) if isinstance(alg, (list, tuple)) else [alg] * len(dbs)
     times, solved, l0 = [], 0, None
     for r in range(warmup + steps):
         for _, _, u0, u, _ in dbs:
@@ -508,8 +560,8 @@ def time_flush(torch, solver, dbs, alg, steps, warmup, stream):
             l0 = solver.launches()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        reqs = [solver.submit(b.family, p, u, alg, ABSTOL, MAXITERS, outs)
-                for b, p, _, u, outs in dbs]
+        reqs = [solver.submit(b.family, p, u, a, ABSTOL, MAXITERS, outs)
+                for (b, p, _, u, outs), a in zip(dbs, algs)]
         solver.flush()
         e1.record(stream)
         sv = sum(solver.wait(q) for q in reqs)
@@ -538,6 +590,88 @@ def sampled_error(dbs, alg, per_batch=4, seed=0):
     return worst
 
 
+TILE_NAMES = {1 << 10: "thread", 1 << 11: "warp", 1 << 12: "cta"}
+
+
+def config0_cubic3(torch, solver, dev, stream, steps, warmup):
+    """1,024 cubic n = 3 instances, plain FP64 Newton: one graph launch per
+    batch (launch-latency bound), analytic and dual-number Jacobians."""
+    dbs = _device_batches(torch, [I.workload_cubic_n3()], dev)
+    res = {"config": "cubic n=3, 1024 instances, plain FP64 Newton, abstol 1e-10, maxiters 50"}
+    with ClockSampler(dev.index or 0) as clk:
+        for name, alg in (("analytic_jacobian", NEWTON | (1 << 9)), ("dual_jacobian", NEWTON)):
+            ms, sv, nl = time_flush(torch, solver, dbs, alg, steps, max(warmup, 3), stream)
+            res[name] = {"ms_per_batch": ms, "us_per_solve": 1e3 * ms / 1024,
+                         "solved_per_s": sv / (ms / 1e3), "solved": sv, "launches": nl}
+    res["clocks"] = clk.summary()
+    for name, alg in (("analytic_jacobian", NEWTON | (1 << 9)), ("dual_jacobian", NEWTON)):
+        time_flush(torch, solver, dbs, alg, 1, 0, stream)
+        res[name]["max_rel_err"] = sampled_error(dbs, alg, 64)
+    return res
+
+
+def config2_uneven(torch, nls, local, dev, stream, steps, warmup, modes=True):
+    """2^18 instances, n log-uniform in 2..32, half cubic and half Bratu,
+    NR + backtracking: every (family, n) bucket in one graph flush, in FP64,
+    in mixed precision, and both precisions in the same flush (each bucket
+    twice); tilings autotuned per bucket and precision.  With `modes`, also
+    the serial launch modes for comparison."""
+    batches = I.workload_uneven()
+    dbs = _device_batches(torch, batches, dev)
+    dbs_m = _device_batches(torch, batches, dev)  # second set of buffers for the joint flush
+    res = {"config": ("2^18 instances, n log-uniform in 2..32, half cubic half Bratu, "
+                      f"NR+backtracking, {len(batches)} (family, n) buckets per precision")}
+    solver = nls.Solver(local, stream)
+    chosen = {}
+    with ClockSampler(local) as clk:
+        for prec, m in (("fp64", 0), ("mixed", MIXED)):
+            alg = LS | m
+            if modes:
+                for mode, persistent, graph in (("direct_serial", 1, 0), ("static_serial", 0, 0)):
+                    solver.set_option(nls.NLS_OPT_PERSISTENT, persistent)
+                    solver.set_option(nls.NLS_OPT_GRAPH, graph)
+                    ms, sv, nl = time_flush(torch, solver, dbs, alg, steps, max(warmup, 3), stream)
+                    res[f"{prec}_{mode}"] = {"ms": ms, "solved_per_s": sv / (ms / 1e3),
+                                             "solved": sv, "launches": nl}
+                solver.set_option(nls.NLS_OPT_PERSISTENT, 1)
+                solver.set_option(nls.NLS_OPT_GRAPH, 1)
+                ms, sv, nl = time_flush(torch, solver, dbs, alg, steps, max(warmup, 3), stream)
+                res[f"{prec}_graph_default_tiling"] = {"ms": ms, "solved_per_s": sv / (ms / 1e3),
+                                                       "solved": sv, "launches": nl}
+            for b, p, u0, u, _ in dbs:
+                u.copy_(u0)
+                chosen[f"{prec}:{b.family}:{b.n}"] = TILE_NAMES[solver.autotune(b.family, p, u, alg)]
+            ms, sv, nl = time_flush(torch, solver, dbs, alg, steps, max(warmup, 3), stream)
+            res[f"{prec}_graph_autotuned"] = {"ms": ms, "solved_per_s": sv / (ms / 1e3),
+                                              "solved": sv, "launches": nl}
+        # both precisions in one flush (the tuning table holds both)
+        algs = [LS] * len(dbs) + [LS | MIXED] * len(dbs_m)
+        ms, sv, nl = time_flush(torch, solver, dbs + dbs_m, algs, steps, max(warmup, 3), stream)
+        res["fp64_and_mixed_one_flush"] = {"ms": ms, "solved_per_s": sv / (ms / 1e3), "solved": sv,
+                                           "launches": nl, "instances": 2 * (1 << 18)}
+    res["clocks"] = clk.summary()
+    res["max_rel_err_fp64"] = sampled_error(dbs, LS, 2)
+    res["max_rel_err_mixed"] = sampled_error(dbs_m, LS | MIXED, 2)
+    res["tiles"] = chosen
+    solver.close()
+    return res
+
+
+def config4_bratu_large(torch, solver, dev, stream, steps, warmup):
+    """16,384 Bratu instances, n uniform in 64..128, trust-region dogleg, one
+    CTA per instance: the FP32 LU with FP64 residual against the FP64 LU."""
+    dbs = _device_batches(torch, I.workload_bratu_large(), dev)
+    res = {"config": ("16,384 Bratu instances, n uniform in 64..128, lambda ~ U[0.5, 3], "
+                      "trust-region dogleg, one CTA per instance")}
+    with ClockSampler(dev.index or 0) as clk:
+        for name, alg in (("fp32_lu_fp64_residual", TR | MIXED), ("fp64_lu", TR)):
+            ms, sv, nl = time_flush(torch, solver, dbs, alg, steps, max(warmup, 3), stream)
+            res[name] = {"ms": ms, "solved_per_s": sv / (ms / 1e3), "solved": sv, "launches": nl}
+            res[name]["max_rel_err"] = sampled_error(dbs, alg, 1)
+    res["clocks"] = clk.summary()
+    return res
+
+
 def run_workload(args, local):
     import torch
     import paper_2403_16341_gb300 as nls
@@ -549,45 +683,9 @@ def run_workload(args, local):
             "data": "synthetic", "unit": "solved systems/s", "results": {}}
     res = line["results"]
     if args.workload == "cubic3":
-        dbs = _device_batches(torch, [I.workload_cubic_n3()], dev)
-        line["config"] = "cubic n=3, 1024 instances, plain FP64 Newton, abstol 1e-10, maxiters 50"
-        for name, alg in (("analytic_jacobian", NEWTON | (1 << 9)), ("dual_jacobian", NEWTON)):
-            ms, sv, nl = time_flush(torch, solver, dbs, alg, args.steps, max(args.warmup, 3), stream)
-            res[name] = {"ms_per_batch": ms, "us_per_solve": 1e3 * ms / 1024,
-                         "solved_per_s": sv / (ms / 1e3), "solved": sv, "launches": nl,
-                         "max_rel_err": sampled_error(dbs, alg, 64)}
+        line["results"] = config0_cubic3(torch, solver, dev, stream, args.steps, args.warmup)
     elif args.workload == "uneven":
-        batches = I.workload_uneven()
-        dbs = _device_batches(torch, batches, dev)
-        line["config"] = ("2^18 instances, n log-uniform in 2..32, half cubic half Bratu, "
-                          f"NR+backtracking, {len(batches)} (family, n) buckets in one flush")
-        for prec, m in (("fp64", 0), ("mixed", MIXED)):
-            alg = LS | m
-            for mode, persistent, graph in (("graph_concurrent", 1, 1), ("direct_serial", 1, 0),
-                                            ("static_serial", 0, 0)):
-                solver.set_option(nls.NLS_OPT_PERSISTENT, persistent)
-                solver.set_option(nls.NLS_OPT_GRAPH, graph)
-                ms, sv, nl = time_flush(torch, solver, dbs, alg, args.steps, max(args.warmup, 3),
-                                        stream)
-                res[f"{prec}_{mode}"] = {"ms": ms, "solved_per_s": sv / (ms / 1e3),
-                                         "solved": sv, "launches": nl}
-            solver.set_option(nls.NLS_OPT_PERSISTENT, 1)
-            solver.set_option(nls.NLS_OPT_GRAPH, 1)
-            # autotuned tiling per bucket, then the concurrent flush again
-            chosen = {}
-            for b, p, u0, u, _ in dbs:
-                u.copy_(u0)
-                chosen[f"{b.family}:{b.n}"] = solver.autotune(b.family, p, u, alg)
-            ms, sv, nl = time_flush(torch, solver, dbs, alg, args.steps, max(args.warmup, 3),
-                                    stream)
-            res[f"{prec}_graph_autotuned"] = {"ms": ms, "solved_per_s": sv / (ms / 1e3),
-                                              "solved": sv, "launches": nl,
-                                              "max_rel_err": sampled_error(dbs, alg, 2),
-                                              "tiles": {k: {1 << 10: "thread", 1 << 11: "warp",
-                                                            1 << 12: "cta"}[v]
-                                                        for k, v in chosen.items()}}
-            solver.close()
-            solver = nls.Solver(local, stream)  # fresh tuning table for the next precision
+        line["results"] = config2_uneven(torch, nls, local, dev, stream, args.steps, args.warmup)
     elif args.workload == "serving":
         line["config"] = "open-loop Poisson arrivals, config-3 request mix"
         # continuous batching on four worker streams, and the serial FIFO mode
@@ -726,17 +824,11 @@ def run_workload(args, local):
                         "ms": ms, "solved": solved, "solved_per_s": solved / (ms / 1e3),
                         "mean_iters": float(outs[1][:b.batch].float().mean().item())}
     elif args.workload == "bratu-large":
-        batches = I.workload_bratu_large()
-        dbs = _device_batches(torch, batches, dev)
-        line["config"] = ("16,384 Bratu instances, n uniform in 64..128, lambda ~ U[0.5, 3], "
-                          "trust-region dogleg, one CTA per instance")
-        for name, alg in (("fp32_lu_fp64_residual", TR | MIXED), ("fp64_lu", TR)):
-            ms, sv, nl = time_flush(torch, solver, dbs, alg, args.steps, max(args.warmup, 3),
-                                    stream)
-            res[name] = {"ms": ms, "solved_per_s": sv / (ms / 1e3), "solved": sv,
-                         "launches": nl, "max_rel_err": sampled_error(dbs, alg, 1)}
+        line["results"] = config4_bratu_large(torch, solver, dev, stream, args.steps, args.warmup)
     else:
         raise SystemExit(f"unknown workload {args.workload}")
+    if "config" not in line:
+        line["config"] = line["results"].pop("config")
     solver.close()
     print(json.dumps(line), flush=True)
 
@@ -764,6 +856,8 @@ def main():
                     choices=["cubic8", "cubic3", "uneven", "bratu-large", "serving", "adjoint",
                              "poly", "next4", "tr-schemes"],
                     help="cubic8: the benchmark step; the others print their own JSON line")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the cubic n=3, uneven and Bratu n=64..128 configurations")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-Newton bar, the end-to-end leg and the CPU baseline")
     args = ap.parse_args()

@@ -135,17 +135,26 @@ enum nls_err {
 /* Per-instance outputs (all DEVICE pointers, each may be NULL = not written):
  * status[k] (nls_inst_status), iters[k] (loop passes), resid_inf[k] =
  * ||F(u_k)||_inf of the returned u_k in FP64, nfev[k] = FP64 residual
- * evaluations used. */
+ * evaluations used, ngrad[k] = trust-region passes that formed the dogleg's
+ * gradient g = J^T F and J g (Eq. 13-14; the thread tiling forms them only
+ * when the Newton step leaves the region, the warp and CTA tilings with
+ * every new Jacobian); 0 for the other algorithms and for NLS_POLYALG. */
 typedef struct nls_outputs {
     int32_t *status;
     int32_t *iters;
     double *resid_inf;
     int32_t *nfev;
+    int32_t *ngrad;
 } nls_outputs;
 
 /* Create a solver context on `device` that enqueues on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  mem_cap_bytes bounds
- * the library-owned device workspace (0 = no cap beyond free memory).
+ * the library-owned device workspace (0 = no cap beyond free memory).  That
+ * workspace is small and grows on demand: a ring of 64 Ki 64-bit counters,
+ * the staging buffers of nls_solve_host, the autotuner's scratch and the
+ * poly-algorithm's gather buffers; the caller's own arrays are never
+ * counted.  (The request server, which holds request state, admits by free
+ * device memory minus a reserve instead: nls_server_create.)
  * Errors: NLS_E_INVALID (out == NULL), NLS_E_CUDA (bad device). */
 int nls_batch_create(nls_handle *out, int device, void *cuda_stream, size_t mem_cap_bytes);
 
@@ -188,7 +197,11 @@ int nls_flush(nls_handle h);
  * timeout_ms on the host (< 0 = no limit, 0 = poll; the device never
  * waits).  On NLS_OK, *solved (may be NULL) = number of its instances with
  * status NLS_SUCCESS.  NLS_E_TIMEOUT if not complete yet (query again);
- * NLS_E_NOTFOUND for an unknown or already released id. */
+ * NLS_E_NOTFOUND for an unknown or already released id.
+ * The per-instance status, iters, resid_inf (and nfev) are not passed here:
+ * they are bound when the request is made (nls_solve's `out`), so the
+ * kernels write them straight into the caller's arrays, with no library
+ * copy, and they are complete once this call returns NLS_OK. */
 int nls_status(nls_handle h, int64_t req, int64_t *solved, int timeout_ms);
 
 /* Synchronous end-to-end variant on HOST buffers: copies params and u
@@ -293,6 +306,24 @@ int nls_server_submit(nls_server_t s, int family, const double *params, double *
  * being on the host.  The ticket is released. */
 int nls_server_wait(nls_server_t s, int64_t ticket, int64_t *solved, double *t_submit,
                     double *t_done, int timeout_ms);
+/* Where a request's time went, for latency analysis.  Host times are on the
+ * server clock (seconds, nls_server_now); device times come from CUDA events
+ * on the request's worker stream (-1 where they could not be taken).  A wave
+ * is the group of requests one dispatcher round admitted onto one worker
+ * stream: their inputs are copied in, then solved by one flush. */
+typedef struct nls_server_timing {
+    double t_submit;   /* nls_server_submit returned the ticket              */
+    double t_admit;    /* the dispatcher admitted it (its state fit)         */
+    double t_launch;   /* its wave's copies and solve were enqueued          */
+    double t_done;     /* the dispatcher saw its results in host memory      */
+    float h2d_ms;      /* device time of its wave's host-to-device copies    */
+    float solve_ms;    /* device time of its wave's solve (one flush)        */
+    float d2h_ms;      /* from the end of that solve to its results copied   */
+    int wave_requests; /* requests in its wave                               */
+} nls_server_timing;
+/* nls_server_wait with the request's stage times in *timing (may be NULL). */
+int nls_server_wait_timed(nls_server_t s, int64_t ticket, int64_t *solved,
+                          nls_server_timing *timing, int timeout_ms);
 /* Seconds since the server was created (monotonic clock). */
 double nls_server_now(nls_server_t s);
 /* Counters: admitted, completed, solved instances, max queue depth, max
@@ -313,7 +344,10 @@ int nls_server_destroy(nls_server_t s);
  * cudaMallocHost or other allocating call.
  *
  * Solves up to NLS_NOALLOC_MAX_GROUPS groups, each of one (family, n) with
- * n <= 8, with the persistent thread-tiled kernel of nls_solve.  Each group
+ * n <= 8, with the persistent thread-tiled kernel of nls_solve.  It runs
+ * Newton, backtracking and the dogleg trust region (with NLS_MIXED,
+ * NLS_ANALYTIC_JAC and NLS_TR_NOCEDAL_WRIGHT as for nls_solve); the other
+ * algorithms of nls_solve give NLS_E_UNSUPPORTED here.  Each group
  * needs two 64-bit counters (its work counter and its solved count); they
  * live in one static device array of NLS_NOALLOC_MAX_GROUPS * 16 bytes that
  * every GPU loading the library holds until the process exits.  All calls
@@ -321,7 +355,11 @@ int nls_server_destroy(nls_server_t s);
  * call, so calls that overlap on the GPU (two streams, two host threads)
  * race: serialise them.  The first call on a device looks up the array's
  * device address and caches it; make that first call before any stream
- * capture.
+ * capture.  The cached address belongs to the device's primary context:
+ * calls after a cudaDeviceReset, or from another context made current on
+ * the same device, are not supported.  A call on a stream that is being
+ * captured must pass solved = NULL (reading the counts waits for the
+ * stream); otherwise it returns NLS_E_INVALID with nothing enqueued.
  *
  * Runs on the current device, enqueued on cuda_stream (NULL = legacy
  * default stream).  Inputs and outputs are the caller's DEVICE pointers,
@@ -329,9 +367,10 @@ int nls_server_destroy(nls_server_t s);
  * NULL the call waits for the stream and stores each group's number of
  * NLS_SUCCESS instances; with NULL it returns once everything is enqueued.
  * Errors: NLS_E_INVALID (ngroups outside 1..NLS_NOALLOC_MAX_GROUPS, NULL
- * pointers, bad abstol / maxiters / algorithm), NLS_E_UNSUPPORTED (n > 8,
- * unknown family, a warp or CTA tiling flag), NLS_E_CUDA; the message is in
- * nls_last_error(NULL). */
+ * pointers, bad abstol / maxiters, an unknown algorithm, solved != NULL
+ * during a capture), NLS_E_UNSUPPORTED (n > 8, unknown family, a warp or
+ * CTA tiling flag, an algorithm other than the three above), NLS_E_CUDA;
+ * the message is in nls_last_error(NULL). */
 #define NLS_NOALLOC_MAX_GROUPS 64
 typedef struct nls_group {
     int family;

@@ -45,7 +45,8 @@ NLS_OPT_DEADLINE_US = 5
 EXPORTED = ("nls_batch_create", "nls_solve", "nls_flush", "nls_status", "nls_solve_host",
             "nls_batch_destroy", "nls_last_error", "nls_launch_count", "nls_set_option",
             "nls_solve_noalloc", "nls_autotune", "nls_tune_save", "nls_tune_load",
-            "nls_server_create", "nls_server_submit", "nls_server_wait", "nls_server_now",
+            "nls_server_create", "nls_server_submit", "nls_server_wait", "nls_server_wait_timed",
+            "nls_server_now",
             "nls_server_stats", "nls_server_destroy", "nls_tune_lookup", "nls_adjoint")
 NLS_NOALLOC_MAX_GROUPS = 64
 
@@ -58,7 +59,15 @@ class NlsError(RuntimeError):
 
 class nls_outputs(ctypes.Structure):
     _fields_ = [("status", ctypes.c_void_p), ("iters", ctypes.c_void_p),
-                ("resid_inf", ctypes.c_void_p), ("nfev", ctypes.c_void_p)]
+                ("resid_inf", ctypes.c_void_p), ("nfev", ctypes.c_void_p),
+                ("ngrad", ctypes.c_void_p)]
+
+
+class nls_server_timing(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_launch", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("h2d_ms", ctypes.c_float), ("solve_ms", ctypes.c_float),
+                ("d2h_ms", ctypes.c_float), ("wave_requests", ctypes.c_int)]
 
 
 class nls_group(ctypes.Structure):
@@ -110,6 +119,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                                    ctypes.POINTER(i64)], i32),
             "nls_server_wait": ([vp, i64, ctypes.POINTER(i64), ctypes.POINTER(dbl),
                                  ctypes.POINTER(dbl), i32], i32),
+            "nls_server_wait_timed": ([vp, i64, ctypes.POINTER(i64),
+                                       ctypes.POINTER(nls_server_timing), i32], i32),
             "nls_server_now": ([vp], dbl),
             "nls_server_stats": ([vp, ctypes.POINTER(i64), i32], i32),
             "nls_server_destroy": ([vp], i32),
@@ -140,15 +151,15 @@ def _check(h, rc: int) -> int:
     return rc
 
 
-def _outs(status=0, iters=0, resid=0, nfev=0):
-    return nls_outputs(status or None, iters or None, resid or None, nfev or None)
+def _outs(status=0, iters=0, resid=0, nfev=0, ngrad=0):
+    return nls_outputs(status or None, iters or None, resid or None, nfev or None, ngrad or None)
 
 
 def nls_solve(h, family, params, u, n, batch, alg, abstol, maxiters, status=0, iters=0,
-              resid_inf=0, nfev=0) -> int:
+              resid_inf=0, nfev=0, ngrad=0) -> int:
     """Enqueue a solve on raw device addresses; returns the request id."""
     req = ctypes.c_int64()
-    out = _outs(status, iters, resid_inf, nfev)
+    out = _outs(status, iters, resid_inf, nfev, ngrad)
     _check(h, load_library().nls_solve(h, family, params or None, u or None, n, batch, alg,
                                        abstol, maxiters, ctypes.byref(out), ctypes.byref(req)))
     return req.value
@@ -169,10 +180,10 @@ def nls_status(h, req: int, timeout_ms: int = -1):
 
 
 def nls_solve_host(h, family, params, u, n, batch, alg, abstol, maxiters, status=0, iters=0,
-                   resid_inf=0, nfev=0) -> int:
+                   resid_inf=0, nfev=0, ngrad=0) -> int:
     """Synchronous solve on raw HOST addresses; returns the solved count."""
     s = ctypes.c_int64(-1)
-    out = _outs(status, iters, resid_inf, nfev)
+    out = _outs(status, iters, resid_inf, nfev, ngrad)
     _check(h, load_library().nls_solve_host(h, family, params or None, u or None, n, batch, alg,
                                             abstol, maxiters, ctypes.byref(out), ctypes.byref(s)))
     return s.value
@@ -255,10 +266,10 @@ def nls_server_create(device: int = 0, mem_budget_bytes: int = 0, streams: int =
 
 
 def nls_server_submit(s, family, params, u, n, batch, alg, abstol, maxiters, status=0, iters=0,
-                      resid_inf=0, nfev=0) -> int:
+                      resid_inf=0, nfev=0, ngrad=0) -> int:
     """Queue a request on raw HOST addresses; returns its ticket."""
     t = ctypes.c_int64()
-    out = _outs(status, iters, resid_inf, nfev)
+    out = _outs(status, iters, resid_inf, nfev, ngrad)
     _gcheck(load_library().nls_server_submit(s, family, params or None, u or None, n, batch, alg,
                                              abstol, maxiters, ctypes.byref(out), ctypes.byref(t)))
     return t.value
@@ -273,6 +284,17 @@ def nls_server_wait(s, ticket: int, timeout_ms: int = -1):
         return None
     _gcheck(rc)
     return sv.value, ts.value, td.value
+
+
+def nls_server_wait_timed(s, ticket: int, timeout_ms: int = -1):
+    """Returns (solved, timing dict) or None on NLS_E_TIMEOUT."""
+    sv, tm = ctypes.c_int64(), nls_server_timing()
+    rc = load_library().nls_server_wait_timed(s, ticket, ctypes.byref(sv), ctypes.byref(tm),
+                                              timeout_ms)
+    if rc == NLS_E_TIMEOUT:
+        return None
+    _gcheck(rc)
+    return sv.value, {f: getattr(tm, f) for f, _ in nls_server_timing._fields_}
 
 
 def nls_server_now(s) -> float:
@@ -326,14 +348,15 @@ class Solver:
     def submit(self, family: int, params, u, alg: int, abstol: float = 1e-10, maxiters: int = 50,
                outputs=None) -> int:
         """Enqueue; ``u`` ([n, B] float64 CUDA, contiguous) is overwritten with the roots.
-        ``outputs`` = (status, iters, resid, nfev) tensors or None."""
+        ``outputs`` = (status, iters, resid, nfev[, ngrad]) tensors (or None
+        entries), or None."""
         n, B = u.shape
-        st = it = rs = nf = 0
+        ptrs = [0, 0, 0, 0, 0]
         if outputs is not None:
-            st, it, rs, nf = (t.data_ptr() if t is not None else 0 for t in outputs)
+            for i, t in enumerate(outputs):
+                ptrs[i] = t.data_ptr() if t is not None else 0
         p = params.data_ptr() if params is not None and params.numel() else 0
-        return nls_solve(self.h, family, p, u.data_ptr(), n, B, alg, abstol, maxiters, st, it,
-                         rs, nf)
+        return nls_solve(self.h, family, p, u.data_ptr(), n, B, alg, abstol, maxiters, *ptrs)
 
     def flush(self) -> None:
         nls_flush(self.h)

@@ -459,6 +459,9 @@ static int launch_poly(nls_batch *h, Request &r)
     if (!a.iters) a.iters = w.fit;
     if (!a.nfev) a.nfev = w.fnf;
     if (!a.resid) a.resid = w.fres;
+    // the stages' gradient counts are not kept: ngrad reads 0 for a poly request
+    if (a.ngrad) NLS_CUDA(h, cudaMemsetAsync(a.ngrad, 0, (size_t)B * 4, st));
+    a.ngrad = nullptr;
     NLS_CUDA(h, cudaMemcpyAsync(w.u0, a.u, (size_t)n * B * 8, cudaMemcpyDeviceToDevice, st));
     NLS_CUDA(h, cudaMemsetAsync(w.ctr, 0, POLY_MAX_STAGES * 3 * 8, st));
     int stages[POLY_MAX_STAGES], ns = 0;
@@ -621,6 +624,7 @@ static int tune_trial(nls_batch *h, const SolveArgs &base, const KernelInfo &k, 
     a.iters = nullptr;
     a.resid = nullptr;
     a.nfev = nullptr;
+    a.ngrad = nullptr;
     int occ = 0;
     int rc = occupancy(h, k, &occ);
     if (rc) return rc;
@@ -708,6 +712,7 @@ static int enqueue(nls_batch *h, int family, const double *params, double *u, in
         r.args.iters = out->iters;
         r.args.resid = out->resid_inf;
         r.args.nfev = out->nfev;
+        r.args.ngrad = out->ngrad;
     }
     if ((alg & NLS_ALG_MASK) == NLS_POLYALG) {
         r.poly = true;
@@ -774,7 +779,7 @@ int nls_solve_host(nls_handle h, int family, const double *params, double *u, in
     NLS_CUDA(h, cudaSetDevice(h->device));
     const size_t E = (size_t)n_params(family, n);
     const size_t bp = E * (size_t)batch * 8, bu = (size_t)n * (size_t)batch * 8, bo = (size_t)batch * 4;
-    const size_t need = bp + bu + 3 * bo + (size_t)batch * 8 + 4 * 256;
+    const size_t need = bp + bu + 4 * bo + (size_t)batch * 8 + 5 * 256;
     if (need > h->stage_bytes) {
         if (h->d_stage) {
             NLS_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -795,6 +800,7 @@ int nls_solve_host(nls_handle h, int family, const double *params, double *u, in
     int32_t *dst = reinterpret_cast<int32_t *>(base + align(bp) + align(bu) + align((size_t)batch * 8));
     int32_t *dit = dst + align(bo) / 4;
     int32_t *dnf = dit + align(bo) / 4;
+    int32_t *dng = dnf + align(bo) / 4;
     // Large batches are pipelined in chunks of instances: chunk c + 1's inputs
     // go up on s_in while chunk c is solved on the handle's stream, and the
     // results of finished chunks come back on s_out; events order the three.
@@ -827,7 +833,8 @@ int nls_solve_host(nls_handle h, int family, const double *params, double *u, in
             NLS_CUDA(h, cudaStreamWaitEvent(h->stream, h->host_ev[2 * c], 0));
         }
         nls_outputs dout{out && out->status ? dst + k0 : nullptr, out && out->iters ? dit + k0 : nullptr,
-                         out && out->resid_inf ? dres + k0 : nullptr, out && out->nfev ? dnf + k0 : nullptr};
+                         out && out->resid_inf ? dres + k0 : nullptr, out && out->nfev ? dnf + k0 : nullptr,
+                         out && out->ngrad ? dng + k0 : nullptr};
         int64_t req = 0;
         rc = enqueue(h, family, bp ? dp + k0 : nullptr, du + k0, n, kc, batch, alg, abstol, maxiters, &dout, &req);
         if (rc) return rc;
@@ -847,6 +854,8 @@ int nls_solve_host(nls_handle h, int family, const double *params, double *u, in
             NLS_CUDA(h, cudaMemcpyAsync(out->iters + k0, dit + k0, kc * 4, cudaMemcpyDeviceToHost, sout));
         if (out && out->nfev)
             NLS_CUDA(h, cudaMemcpyAsync(out->nfev + k0, dnf + k0, kc * 4, cudaMemcpyDeviceToHost, sout));
+        if (out && out->ngrad)
+            NLS_CUDA(h, cudaMemcpyAsync(out->ngrad + k0, dng + k0, kc * 4, cudaMemcpyDeviceToHost, sout));
         if (out && out->resid_inf)
             NLS_CUDA(h, cudaMemcpyAsync(out->resid_inf + k0, dres + k0, kc * 8, cudaMemcpyDeviceToHost, sout));
     }

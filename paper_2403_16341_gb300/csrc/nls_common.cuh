@@ -60,6 +60,7 @@ struct SolveArgs {
     int32_t *iters;
     double *resid;
     int32_t *nfev;
+    int32_t *ngrad;              // trust region: passes that formed g = J^T F (may be null)
     unsigned long long *solved;  // += #SUCCESS (may be null)
     unsigned long long *counter; // work counter for persistent launches (null = static)
     int refill_below;            // persistent: refill idle lanes when live lanes <= this

@@ -69,6 +69,7 @@ struct CtaSolver {
     double lam; // Bratu lambda
     double fF, Delta;
     int it, nfev, rej, status;
+    int ngrad; // trust region: passes that formed g = J^T F and J g
     bool need_jac;
     uint64_t fmag;
 
@@ -472,6 +473,7 @@ struct CtaSolver {
         nfev = 1;
         it = 0;
         rej = 0;
+        ngrad = 0;
         Delta = TR_DELTA0;
         need_jac = true;
         status = ST_RUNNING;
@@ -491,6 +493,7 @@ struct CtaSolver {
             if (tid < n) sm.Fp[tid] = P(sm.F[tid]);
             __syncthreads();
             if (A.alg == ALG_TRUST_DOGLEG) {
+                ++ngrad;
                 // g = J^T F and J g
 #pragma unroll
                 for (int bb = 0; bb < R; ++bb) {
@@ -653,6 +656,7 @@ struct CtaSolver {
             if (A.iters) A.iters[k] = it;
             if (A.resid) A.resid[k] = bits_to_double(fmag);
             if (A.nfev) A.nfev[k] = nfev;
+            if (A.ngrad) A.ngrad[k] = ngrad;
             if (A.solved && status == ST_SUCCESS) atomicAdd(A.solved, 1ull);
         }
     }

@@ -40,7 +40,11 @@ int err(int code, const char *fmt, ...)
 
 // Device address of the scratch array on the current device.  The host-side
 // name g_noalloc_scratch is only a stand-in for the symbol, so the address
-// is looked up once per device (with that device current) and cached.
+// is looked up once per device (with that device current) and cached.  The
+// cache belongs to the device's primary context (the one the runtime API
+// uses): a cudaDeviceReset between calls, or a caller that made another
+// context current on that device, would leave a stale address here, and
+// neither is supported.
 int scratch_on_current_device(unsigned long long **out)
 {
     int dev = -1;
@@ -72,7 +76,11 @@ extern "C" int nls_solve_noalloc(void *cuda_stream, const nls_group *groups, int
     if (!groups) return err(NLS_E_INVALID, "groups is NULL");
     if (!(abstol >= 0.0) || !std::isfinite(abstol)) return err(NLS_E_INVALID, "abstol must be finite and >= 0");
     if (maxiters < 0) return err(NLS_E_INVALID, "negative maxiters");
-    if ((alg & NLS_ALG_MASK) > NLS_TRUST_DOGLEG) return err(NLS_E_INVALID, "unknown algorithm %d", alg & NLS_ALG_MASK);
+    if ((alg & NLS_ALG_MASK) > NLS_MOD_BROYDEN) return err(NLS_E_INVALID, "unknown algorithm %d", alg & NLS_ALG_MASK);
+    if ((alg & NLS_ALG_MASK) > NLS_TRUST_DOGLEG)
+        return err(NLS_E_UNSUPPORTED,
+                   "algorithm %d: nls_solve_noalloc runs Newton, backtracking and dogleg only",
+                   alg & NLS_ALG_MASK);
     if ((alg & NLS_TR_NOCEDAL_WRIGHT) && (alg & NLS_ALG_MASK) != NLS_TRUST_DOGLEG)
         return err(NLS_E_INVALID, "NLS_TR_NOCEDAL_WRIGHT needs NLS_TRUST_DOGLEG");
     if (alg & ~(NLS_ALG_MASK | NLS_MIXED | NLS_ANALYTIC_JAC | NLS_TILE_THREAD | NLS_TR_NOCEDAL_WRIGHT))
@@ -89,10 +97,18 @@ extern "C" int nls_solve_noalloc(void *cuda_stream, const nls_group *groups, int
         kern[g] = nls::thread_kernel(q.family, q.n, (alg & NLS_MIXED) != 0, (alg & NLS_ANALYTIC_JAC) != 0);
         if (!kern[g].launch) return err(NLS_E_UNSUPPORTED, "group %d: unknown family %d", g, q.family);
     }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (solved) {
+        // reading the counts back waits for the stream, which a capture forbids
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaError_t ce = cudaStreamIsCapturing(st, &cap);
+        if (ce != cudaSuccess) return err(NLS_E_CUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(ce));
+        if (cap != cudaStreamCaptureStatusNone)
+            return err(NLS_E_INVALID, "solved must be NULL while the stream is being captured");
+    }
     unsigned long long *scratch = nullptr;
     int rc = scratch_on_current_device(&scratch);
     if (rc) return rc;
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -116,6 +132,7 @@ extern "C" int nls_solve_noalloc(void *cuda_stream, const nls_group *groups, int
         a.iters = q.out.iters;
         a.resid = q.out.resid_inf;
         a.nfev = q.out.nfev;
+        a.ngrad = q.out.ngrad;
         a.solved = scratch + 2 * g;
         a.counter = scratch + 2 * g + 1;
         a.refill_below = 24;

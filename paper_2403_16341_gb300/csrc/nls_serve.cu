@@ -82,6 +82,24 @@ struct Arena {
     }
 };
 
+// Timing events of one worker wave: before its input copies, before its
+// solve launch, after it.
+struct WaveEvents {
+    cudaEvent_t a = nullptr, b = nullptr, c = nullptr;
+    bool ok = false;
+    WaveEvents()
+    {
+        ok = cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess &&
+             cudaEventCreate(&c) == cudaSuccess;
+    }
+    ~WaveEvents()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        if (c) cudaEventDestroy(c);
+    }
+};
+
 struct Ticket {
     int64_t id = 0;
     int family = 0, n = 0, alg = 0, maxiters = 0;
@@ -94,9 +112,13 @@ struct Ticket {
     int worker = -1;
     int64_t req = 0;
     cudaEvent_t ev = nullptr;
-    double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+    double t_submit = 0.0, t_admit = 0.0, t_launch = 0.0, t_done = 0.0;
+    std::shared_ptr<WaveEvents> wave;
+    float h2d_ms = -1.f, solve_ms = -1.f, d2h_ms = -1.f;
+    int wave_requests = 0;
     int64_t solved = -1;
     int state = 0; // 0 queued, 1 in flight, 2 done, 3 failed
+    bool failed = false; // enqueueing failed; state becomes 3 once its copies are done
     std::string err;
 };
 
@@ -150,13 +172,13 @@ static size_t n_params(int family, int n)
 static size_t ticket_bytes(int family, int n, int64_t batch)
 {
     return al256(n_params(family, n) * batch * 8) + al256(size_t(n) * batch * 8) + al256(batch * 8) +
-           3 * al256(batch * 4);
+           4 * al256(batch * 4);
 }
 
-// Device layout of a ticket's arena block: params, u, resid, status, iters, nfev.
+// Device layout of a ticket's arena block: params, u, resid, status, iters, nfev, ngrad.
 struct Layout {
     double *p, *u, *resid;
-    int32_t *status, *iters, *nfev;
+    int32_t *status, *iters, *nfev, *ngrad;
 };
 
 static Layout layout(const Ticket &t, char *arena)
@@ -175,6 +197,8 @@ static Layout layout(const Ticket &t, char *arena)
     L.iters = reinterpret_cast<int32_t *>(c);
     c += al256(t.batch * 4);
     L.nfev = reinterpret_cast<int32_t *>(c);
+    c += al256(t.batch * 4);
+    L.ngrad = reinterpret_cast<int32_t *>(c);
     return L;
 }
 
@@ -184,6 +208,7 @@ static void dispatcher(nls_server *s)
 {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
+    int idle_polls = 0;
     for (;;) {
         // ---- admit waiting requests in arrival order while they fit
         std::vector<std::vector<std::shared_ptr<Ticket>>> wave(s->workers.size());
@@ -209,6 +234,8 @@ static void dispatcher(nls_server *s)
             if (wave[w].empty()) continue;
             nls_handle h = s->workers[w];
             cudaStream_t st = s->streams[w];
+            auto W = std::make_shared<WaveEvents>();
+            if (W->ok) cudaEventRecord(W->a, st);
             for (auto &t : wave[w]) {
                 const size_t E = n_params(t->family, t->n);
                 const Layout L = layout(*t, s->arena_d);
@@ -216,61 +243,93 @@ static void dispatcher(nls_server *s)
                 if (E && t->batch) e = cudaMemcpyAsync(L.p, t->h_params, E * t->batch * 8, cudaMemcpyHostToDevice, st);
                 if (e == cudaSuccess && t->batch)
                     e = cudaMemcpyAsync(L.u, t->h_u, size_t(t->n) * t->batch * 8, cudaMemcpyHostToDevice, st);
-                nls_outputs dout{L.status, L.iters, L.resid, L.nfev};
+                nls_outputs dout{L.status, L.iters, L.resid, L.nfev, L.ngrad};
                 int rc = e == cudaSuccess ? nls_solve(h, t->family, E ? L.p : nullptr, L.u, t->n, t->batch, t->alg,
                                                       t->abstol, t->maxiters, &dout, &t->req)
                                           : NLS_E_CUDA;
                 if (rc) {
-                    t->state = 3;
+                    t->failed = true;
                     t->err = e != cudaSuccess ? cudaGetErrorString(e) : nls_last_error(h);
                 }
             }
+            if (W->ok) cudaEventRecord(W->b, st);
             nls_flush(h);
+            if (W->ok) cudaEventRecord(W->c, st);
+            const double t_launch = s->now();
             for (auto &t : wave[w]) {
-                if (t->state == 3) continue;
+                t->t_launch = t_launch;
+                t->wave_requests = (int)wave[w].size();
+                if (W->ok) t->wave = W;
+                if (t->failed) {
+                    // its input copies may already be queued on the stream: the
+                    // arena block is released only once the stream has passed them
+                    if (cudaEventCreateWithFlags(&t->ev, cudaEventDisableTiming) != cudaSuccess ||
+                        cudaEventRecord(t->ev, st) != cudaSuccess) {
+                        if (t->ev) cudaEventDestroy(t->ev);
+                        t->ev = nullptr;
+                        cudaStreamSynchronize(st);
+                    }
+                    continue;
+                }
                 const Layout L = layout(*t, s->arena_d);
                 if (t->batch) {
                     cudaMemcpyAsync(t->h_u, L.u, size_t(t->n) * t->batch * 8, cudaMemcpyDeviceToHost, st);
                     if (t->h_out.status) cudaMemcpyAsync(t->h_out.status, L.status, t->batch * 4, cudaMemcpyDeviceToHost, st);
                     if (t->h_out.iters) cudaMemcpyAsync(t->h_out.iters, L.iters, t->batch * 4, cudaMemcpyDeviceToHost, st);
                     if (t->h_out.nfev) cudaMemcpyAsync(t->h_out.nfev, L.nfev, t->batch * 4, cudaMemcpyDeviceToHost, st);
+                    if (t->h_out.ngrad)
+                        cudaMemcpyAsync(t->h_out.ngrad, L.ngrad, t->batch * 4, cudaMemcpyDeviceToHost, st);
                     if (t->h_out.resid_inf)
                         cudaMemcpyAsync(t->h_out.resid_inf, L.resid, t->batch * 8, cudaMemcpyDeviceToHost, st);
                 }
-                cudaEventCreateWithFlags(&t->ev, cudaEventDisableTiming);
+                if (t->wave) cudaEventCreate(&t->ev); // timed: the wave's events are its base
+                else cudaEventCreateWithFlags(&t->ev, cudaEventDisableTiming);
                 cudaEventRecord(t->ev, st);
             }
         }
         lk.lock();
+        bool retire_failed = false;
         for (size_t w = 0; w < wave.size(); ++w) {
             if (!wave[w].empty()) ++s->waves;
             for (auto &t : wave[w]) {
-                if (t->state == 3) {
+                if (t->failed && !t->ev) { // the stream was synchronised above
                     s->arena.release(t->off, t->bytes);
                     --s->load[t->worker];
                     t->t_done = s->now();
+                    t->state = 3;
+                    retire_failed = true;
                     continue;
                 }
                 s->inflight.push_back(t);
             }
         }
         s->max_inflight = std::max<int64_t>(s->max_inflight, (int64_t)s->inflight.size());
-        // ---- retire completed requests
-        bool retired = false;
+        // ---- retire completed requests (and failed ones whose copies are done)
+        bool retired = retire_failed;
         for (size_t i = 0; i < s->inflight.size();) {
             auto t = s->inflight[i];
             if (cudaEventQuery(t->ev) == cudaSuccess) {
-                int64_t sv = -1;
-                nls_status(s->workers[t->worker], t->req, &sv, 0);
+                if (t->wave && !t->failed) {
+                    cudaEventElapsedTime(&t->h2d_ms, t->wave->a, t->wave->b);
+                    cudaEventElapsedTime(&t->solve_ms, t->wave->b, t->wave->c);
+                    cudaEventElapsedTime(&t->d2h_ms, t->wave->c, t->ev);
+                }
+                t->wave.reset();
                 cudaEventDestroy(t->ev);
                 t->ev = nullptr;
-                t->solved = sv;
                 t->t_done = s->now();
-                t->state = 2;
                 s->arena.release(t->off, t->bytes);
                 --s->load[t->worker];
-                ++s->completed;
-                s->solved += std::max<int64_t>(sv, 0);
+                if (t->failed) {
+                    t->state = 3;
+                } else {
+                    int64_t sv = -1;
+                    nls_status(s->workers[t->worker], t->req, &sv, 0);
+                    t->solved = sv;
+                    t->state = 2;
+                    ++s->completed;
+                    s->solved += std::max<int64_t>(sv, 0);
+                }
                 s->inflight[i] = s->inflight.back();
                 s->inflight.pop_back();
                 retired = true;
@@ -282,11 +341,18 @@ static void dispatcher(nls_server *s)
         if (s->stop && s->queue.empty() && s->inflight.empty()) break;
         if (s->inflight.empty() && s->queue.empty()) {
             s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+            idle_polls = 0;
         } else if (!retired) {
-            // poll completions at ~20 us granularity while work is in flight
+            // poll completions while work is in flight: yield (a few microseconds
+            // per round) for the first ~2000 rounds after the last completion,
+            // then 20 us sleeps (which the kernel's timer slack stretches to
+            // 60-80 us), so a long solve does not keep a core spinning
             lk.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            if (++idle_polls < 2000) std::this_thread::yield();
+            else std::this_thread::sleep_for(std::chrono::microseconds(20));
             lk.lock();
+        } else {
+            idle_polls = 0;
         }
     }
 }
@@ -365,8 +431,8 @@ int nls_server_submit(nls_server_t s, int family, const double *params, double *
     return NLS_OK;
 }
 
-int nls_server_wait(nls_server_t s, int64_t ticket, int64_t *solved, double *t_submit, double *t_done,
-                    int timeout_ms)
+int nls_server_wait_timed(nls_server_t s, int64_t ticket, int64_t *solved, nls_server_timing *timing,
+                          int timeout_ms)
 {
     if (!s) return serr(NLS_E_INVALID, "NULL server");
     std::unique_lock<std::mutex> lk(s->mu);
@@ -380,9 +446,29 @@ int nls_server_wait(nls_server_t s, int64_t ticket, int64_t *solved, double *t_s
     s->tickets.erase(it);
     if (t->state == 3) return serr(NLS_E_CUDA, "ticket %lld failed: %s", (long long)ticket, t->err.c_str());
     if (solved) *solved = t->solved;
-    if (t_submit) *t_submit = t->t_submit;
-    if (t_done) *t_done = t->t_done;
+    if (timing) {
+        timing->t_submit = t->t_submit;
+        timing->t_admit = t->t_admit;
+        timing->t_launch = t->t_launch;
+        timing->t_done = t->t_done;
+        timing->h2d_ms = t->h2d_ms;
+        timing->solve_ms = t->solve_ms;
+        timing->d2h_ms = t->d2h_ms;
+        timing->wave_requests = t->wave_requests;
+    }
     return NLS_OK;
+}
+
+int nls_server_wait(nls_server_t s, int64_t ticket, int64_t *solved, double *t_submit, double *t_done,
+                    int timeout_ms)
+{
+    nls_server_timing tm{};
+    const int rc = nls_server_wait_timed(s, ticket, solved, &tm, timeout_ms);
+    if (rc == NLS_OK) {
+        if (t_submit) *t_submit = tm.t_submit;
+        if (t_done) *t_done = tm.t_done;
+    }
+    return rc;
 }
 
 double nls_server_now(nls_server_t s) { return s ? s->now() : 0.0; }

@@ -227,6 +227,7 @@ struct ThreadSolver {
     }
     double fF, Delta;
     int it, nfev, rej, status;
+    int ngrad;   // trust region: passes that formed g and J g
     bool need_jac;
     bool have_g; // trust region: g = J^T F and J g formed for the current J
 
@@ -238,6 +239,7 @@ struct ThreadSolver {
         nfev = 1;
         it = 0;
         rej = 0;
+        ngrad = 0;
         Delta = TR_DELTA0;
         need_jac = true;
         have_g = false;
@@ -257,6 +259,7 @@ struct ThreadSolver {
         if (a.iters) a.iters[k] = it;
         if (a.resid) a.resid[k] = bits_to_double(max_mag_bits(F));
         if (a.nfev) a.nfev[k] = nfev;
+        if (a.ngrad) a.ngrad[k] = ngrad;
     }
 
     // g = J^T Fp and, with jg, J g.
@@ -364,6 +367,7 @@ struct ThreadSolver {
                     jacobian(pv, u, J);
                     gradient(J, true);
                     have_g = true;
+                    ++ngrad;
                 }
                 P gg = P(0), JgJg = P(0);
 #pragma unroll

@@ -67,6 +67,7 @@ struct ThreadSolverBase {
         if (a.iters) a.iters[k] = it;
         if (a.resid) a.resid[k] = bits_to_double(max_mag_bits(F));
         if (a.nfev) a.nfev[k] = nfev;
+        if (a.ngrad) a.ngrad[k] = 0;
     }
 
     // convergence test after a pass (Sec. 2.1)

@@ -80,6 +80,7 @@ struct WarpSolver {
     P g, Jg, Fp;
     double fF, Delta;
     int it, nfev, rej, status;
+    int ngrad; // trust region: passes that formed g = J^T F and J g
     bool need_jac;
 
     NLS_DI bool row_live() const { return r < n; }
@@ -276,6 +277,7 @@ struct WarpSolver {
         nfev = 1;
         it = 0;
         rej = 0;
+        ngrad = 0;
         Delta = TR_DELTA0;
         need_jac = true;
         fF = seg_sum<L>(F * F, mask);
@@ -295,6 +297,7 @@ struct WarpSolver {
             if (a.iters) a.iters[k] = it;
             if (a.resid) a.resid[k] = bits_to_double(fmag);
             if (a.nfev) a.nfev[k] = nfev;
+            if (a.ngrad) a.ngrad[k] = ngrad;
         }
     }
 
@@ -326,7 +329,10 @@ struct WarpSolver {
 #pragma unroll
                 for (int j = 0; j < L; ++j) t = fma(a[j], sm.vec[j], t);
                 __syncwarp();
-                if (fresh) Jg = t;
+                if (fresh) {
+                    Jg = t;
+                    ++ngrad;
+                }
             }
             P b = -fp;
             const bool ok = lu_solve(a, b, sm);

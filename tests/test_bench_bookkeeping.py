@@ -34,6 +34,12 @@ def test_flops_per_residual_and_pass(bench):
     assert bench.algorithmic_fp64_flops(n, TR, iters, nfev) == pytest.approx(6 * res + 5 * (per_pass + 80))
     # mixed mode: the Jacobian and LU are FP32, only the residual side counts
     assert bench.algorithmic_fp64_flops(n, TR | MIXED, iters, nfev) == pytest.approx(6 * res)
+    # the passes that formed g = J^T F and J g add 2n^2 each (FP64 mode only)
+    ngrad = np.array([3])
+    assert bench.algorithmic_fp64_flops(n, TR, iters, nfev, ngrad) == pytest.approx(
+        6 * res + 5 * (per_pass + 80) + 3 * 256)
+    assert bench.algorithmic_fp64_flops(n, TR | MIXED, iters, nfev, ngrad) == pytest.approx(6 * res)
+    assert bench.algorithmic_fp64_flops(n, LS, iters, nfev, ngrad) == pytest.approx(6 * res + 5 * per_pass)
 
 
 def test_traffic_is_tied_to_the_kernel_sources(bench, monkeypatch):

@@ -1,20 +1,23 @@
 """GPU parity of the Potra-Ptak (Eq. 4), Halley (Eq. 3), Broyden and modified
-Broyden (Tab. 1) thread kernels against the FP64 oracle, through the C ABI.
+Broyden (Tab. 1) kernels against the FP64 oracle, through the C ABI.
 
 Tolerances are those of the Newton kernels (1e-9 FP64, 1e-8 mixed,
-relative to max(1, ||u*||_inf), or the conditioning bound).  Statuses are
-compared exactly in FP64 where the iteration is stable; the chaotic rule
-(instances both sides solve agree, every reported success passes the
-residual test) applies where the outcome depends on rounding: Broyden from
-the identity and Potra-Ptak cycling far from the root.  The GPU keeps B^-1
-by Sherman-Morrison where the oracle refactors B, so Broyden is compared by
-outcome, not by bits."""
+relative to max(1, ||u*||_inf), or the conditioning bound).  Statuses
+follow the rule of each case (status_rule below, tests/parity.py):
+Halley's statuses are compared exactly; the local methods (Potra-Ptak and
+the two Broydens, which can cycle or diverge) by their solved sets, which
+must equal the oracle's in FP64 apart from instances the oracle ends in
+its last five passes and instances whose outcome rounding decides (shown
+by the oracle's own per-pass jitter); Rosenbrock from U[0,1)^n is
+rounding-chaotic for every method.  The GPU keeps
+B^-1 by Sherman-Morrison where the oracle refactors B, so Broyden is
+compared by outcome and root, not by bits."""
 import numpy as np
 import pytest
 
 import oracle as O
 from paper_2403_16341_gb300 import inputs as I
-from tests.parity import check_parity, gpu_solve, oracle_solve
+from tests.parity import check_parity, gpu_solve, late_instances, oracle_solve
 
 pytestmark = pytest.mark.gpu
 
@@ -42,13 +45,16 @@ def family_batch(family, n, B):
     return I.rosenbrock_batch(n, B, seed=0)
 
 
-def chaotic_case(family, alg):
-    # Broyden from B_0 = I is a local method started far away on Bratu and
-    # Rosenbrock (the oracle solves 0-7% of them); Potra-Ptak's frozen
-    # Jacobian cycles on some square instances started at u0 = 1
-    return (alg == BROYDEN) or (alg == PP and family == I.FAMILY_SQUARE) \
-        or (alg == MOD_BROYDEN and family == I.FAMILY_ROSENBROCK) \
-        or (alg == HALLEY and family == I.FAMILY_ROSENBROCK)
+def status_rule(family, alg):
+    """The status rule of check_parity for one case: the generalized
+    Rosenbrock function from U[0,1)^n is rounding-chaotic for every method
+    here; the local methods (Potra-Ptak, Broyden, modified Broyden) are
+    compared by their solved sets; Halley exactly."""
+    if family == I.FAMILY_ROSENBROCK:
+        return "chaotic"
+    if alg in (PP, BROYDEN, MOD_BROYDEN):
+        return "success_set"
+    return "exact"
 
 
 @pytest.mark.parametrize("family", [I.FAMILY_CUBIC, I.FAMILY_BRATU, I.FAMILY_SQUARE,
@@ -62,7 +68,7 @@ def test_families_all_sizes(solver, family, n, alg, mixed):
     b = family_batch(family, n, 97)
     g = gpu_solve(solver, b, alg | (MIXED if mixed else 0))
     o = oracle_solve(b, alg)
-    check_parity(b, g, o, mixed, chaotic=chaotic_case(family, alg) or mixed and alg == BROYDEN)
+    check_parity(b, g, o, mixed, rule=status_rule(family, alg), alg=alg)
 
 
 @pytest.mark.parametrize("alg", [HALLEY, MOD_BROYDEN, PP])
@@ -72,7 +78,7 @@ def test_cubic_n8_parity_ragged(solver, alg, mixed):
     b = I.cubic_batch(8, 4099, config_id=1, b_half_width=5.0)
     g = gpu_solve(solver, b, alg | (MIXED if mixed else 0))
     o = oracle_solve(b, alg)
-    err = check_parity(b, g, o, mixed, chaotic=(alg == PP))
+    err = check_parity(b, g, o, mixed, rule=status_rule(b.family, alg), alg=alg)
     if alg != PP:
         assert g["solved"] == b.batch
     if not mixed and alg != PP:
@@ -156,39 +162,46 @@ def test_unsupported_combinations(solver):
     assert e.value.code == nls.NLS_E_INVALID
 
 
-@pytest.mark.parametrize("alg", [HALLEY, MOD_BROYDEN])
-def test_full_size_sampled(solver, alg):
+@pytest.mark.parametrize("alg", [HALLEY, MOD_BROYDEN, PP, BROYDEN])
+def test_full_size(solver, alg):
     # the cubic n = 8, 2^20 workload in the launch mode the benchmark uses
-    # (autotuned), sampled against the oracle instance by instance
+    # (autotuned): the solved set against the oracle's over the whole batch
+    # (Halley: every instance solved; the local methods: the success_set
+    # rule), the roots on a sample of 300 instances
+    import torch
     b = I.workload_cubic_n8()
+    o = oracle_solve(b, alg, threads=16)
+    ok_o = o["status"] == 0
     for mixed in (False, True):
+        late = late_instances(o, margin=10 if mixed else 5)
         a = alg | (MIXED if mixed else 0)
-        import torch
         p = torch.from_numpy(b.params).cuda()
         u0 = torch.from_numpy(b.u0).cuda()
         solver.autotune(b.family, p, u0.clone(), a, 1e-10, 50)
         g = gpu_solve(solver, b, a)
+        ok_g = g["status"] == 0
         if alg == HALLEY:
-            assert g["solved"] == b.batch
+            assert g["solved"] == b.batch and ok_o.all()
         else:
-            # B^-1 by Sherman-Morrison rounds differently from the oracle's
-            # refactored B: an instance that needs close to maxiters passes
-            # may end on either side.  Each GPU failure must be one the
-            # oracle also fails or solves only late.
-            bad = np.nonzero(g["status"] != 0)[0]
-            assert bad.size <= 16, bad.size
-            if bad.size:
-                sub = I.Batch(b.family, b.n, np.ascontiguousarray(b.params[:, bad]),
-                              np.ascontiguousarray(b.u0[:, bad]))
-                o = oracle_solve(sub, alg)
-                assert ((o["status"] != 0) | (o["iters"] >= 30)).all(), (o["status"], o["iters"])
+            bad = (ok_o & ~ok_g) if mixed else (ok_o != ok_g)
+            sel = np.nonzero(bad & ~late)[0]
+            print(f"alg {alg} mixed {mixed}: solved gpu {int(ok_g.sum())} oracle {int(ok_o.sum())}, "
+                  f"{int((bad & late).sum())} late differences, {sel.size} others")
+            if sel.size:
+                # every other difference must be judged by the rule on its own
+                sub = I.Batch(b.family, b.n, np.ascontiguousarray(b.params[:, sel]),
+                              np.ascontiguousarray(b.u0[:, sel]))
+                gs = {k: (v[..., sel] if isinstance(v, np.ndarray) else v) for k, v in g.items()}
+                gs["solved"] = int((gs["status"] == 0).sum())
+                os_ = {k: v[..., sel] for k, v in o.items()}
+                check_parity(sub, gs, os_, mixed, rule="success_set", alg=alg)
         rng = np.random.default_rng(7)
         idx = np.sort(rng.choice(b.batch, 300, replace=False))
         sub = I.Batch(b.family, b.n, np.ascontiguousarray(b.params[:, idx]), np.ascontiguousarray(b.u0[:, idx]))
-        o = oracle_solve(sub, alg)
         gs = {k: (v[..., idx] if isinstance(v, np.ndarray) else v) for k, v in g.items()}
         gs["solved"] = int((gs["status"] == 0).sum())
-        check_parity(sub, gs, o, mixed, chaotic=(alg == MOD_BROYDEN))
+        os_ = {k: v[..., idx] for k, v in o.items()}
+        check_parity(sub, gs, os_, mixed, rule=status_rule(b.family, alg), alg=alg)
 
 
 @pytest.mark.parametrize("family", [I.FAMILY_CUBIC, I.FAMILY_BRATU, I.FAMILY_SQUARE,
@@ -198,16 +211,12 @@ def test_full_size_sampled(solver, alg):
 @pytest.mark.parametrize("mixed", [False, True])
 def test_warp_tiling(solver, family, n, alg, mixed):
     # 8 < n <= 32: one instance per segment of 16 or 32 lanes; Rosenbrock from
-    # U[0, 1)^n is rounding-chaotic at n >= 12 for every method here (as for
-    # plain Newton at n >= 13), and Potra-Ptak's starts there sit at the edge
-    # of its basin already at n = 9 (76% solved at n = 12), so the FP32 LU of
-    # mixed mode can move an instance across it
+    # U[0, 1)^n is rounding-decided for every method here (Potra-Ptak's starts
+    # sit at the edge of its basin already at n = 9, 76% solved at n = 12)
     b = family_batch(family, n, 67)
     g = gpu_solve(solver, b, alg | (MIXED if mixed else 0))
     o = oracle_solve(b, alg)
-    chaotic = (chaotic_case(family, alg) or (mixed and alg == BROYDEN)
-               or (family == I.FAMILY_ROSENBROCK and (n >= 12 or mixed)))
-    check_parity(b, g, o, mixed, chaotic=chaotic)
+    check_parity(b, g, o, mixed, rule=status_rule(family, alg), alg=alg)
 
 
 @pytest.mark.parametrize("alg", NEXT4)
@@ -216,7 +225,7 @@ def test_warp_tiling_forced_small_n(solver, alg):
     b = I.cubic_batch(5, 131, config_id=2)
     g = gpu_solve(solver, b, alg | TILE_WARP)
     o = oracle_solve(b, alg)
-    check_parity(b, g, o, False, chaotic=(alg == BROYDEN))
+    check_parity(b, g, o, False, rule=status_rule(b.family, alg), alg=alg)
 
 
 @pytest.mark.parametrize("family", [I.FAMILY_CUBIC, I.FAMILY_BRATU, I.FAMILY_SQUARE])
@@ -230,7 +239,7 @@ def test_cta_tiling(solver, family, n, alg, mixed):
     b = family_batch(family, n, 37)
     g = gpu_solve(solver, b, alg | (MIXED if mixed else 0))
     o = oracle_solve(b, alg)
-    check_parity(b, g, o, mixed, chaotic=(alg == BROYDEN))
+    check_parity(b, g, o, mixed, rule=status_rule(family, alg), alg=alg)
     if alg != BROYDEN:
         assert g["solved"] == b.batch
 
@@ -241,5 +250,5 @@ def test_cta_tiling_forced_small_n(solver, alg):
     b = I.cubic_batch(12, 45, config_id=2)
     g = gpu_solve(solver, b, alg | TILE_CTA)
     o = oracle_solve(b, alg)
-    check_parity(b, g, o, False, chaotic=(alg == BROYDEN))
+    check_parity(b, g, o, False, rule=status_rule(b.family, alg), alg=alg)
 

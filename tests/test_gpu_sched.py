@@ -25,9 +25,12 @@ def solver():
 
 
 def submit_all(solver, batches, alg):
+    """Every batch in one flush; `alg` is one algorithm word for all of them
+    or a list with one per batch (precision may differ between buckets)."""
     import torch
+    algs = list(alg) if isinstance(alg, (list, tuple)) else [alg] * len(batches)
     held, reqs = [], []
-    for b in batches:
+    for b, alg in zip(batches, algs):
         p = torch.from_numpy(np.ascontiguousarray(b.params)).cuda() if b.params.size else None
         u = torch.from_numpy(np.ascontiguousarray(b.u0)).cuda()
         st = torch.empty(b.batch, dtype=torch.int32, device="cuda")
@@ -50,6 +53,24 @@ def test_mix_equals_alone(solver, alg):
         np.testing.assert_array_equal(st, alone["status"])
         np.testing.assert_array_equal(it, alone["iters"])
         assert s == alone["solved"]
+
+
+@pytest.mark.parametrize("base", [LS, TR])
+def test_fp64_and_mixed_buckets_in_one_flush(solver, base):
+    # every bucket of an uneven batch twice, once in FP64 and once in mixed
+    # precision, plus a per-bucket choice (mixed for the odd buckets), all in
+    # one flush: each request equals the same request solved alone
+    batches = I.uneven_batches(1 << 13, config_id=2)
+    both = batches + batches + batches
+    algs = ([base] * len(batches) + [base | MIXED] * len(batches)
+            + [base | (MIXED if i % 2 else 0) for i in range(len(batches))])
+    res = submit_all(solver, both, algs)
+    for b, a, (u, st, it, s) in zip(both, algs, res):
+        alone = gpu_solve(solver, b, a)
+        np.testing.assert_array_equal(u, alone["u"])
+        np.testing.assert_array_equal(st, alone["status"])
+        np.testing.assert_array_equal(it, alone["iters"])
+        assert s == alone["solved"] == b.batch
 
 
 def test_graph_and_direct_agree(solver):
@@ -131,6 +152,25 @@ def test_uneven_full_size(solver, mixed):
         err = np.abs(u[:, idx] - ref).max(axis=0) / np.maximum(1, np.abs(ref).max(axis=0))
         assert err.max() <= (1e-8 if mixed else 1e-9)
     assert total == 1 << 18
+
+
+def test_uneven_full_size_fp64_and_mixed_in_one_flush(solver):
+    # the 2^18-instance uneven set solved in FP64 and in mixed precision in
+    # one flush (124 requests): every instance solved in both precisions, a
+    # sample of each bucket within the parity tolerance of its precision
+    batches = I.workload_uneven()
+    algs = [LS] * len(batches) + [LS | MIXED] * len(batches)
+    res = submit_all(solver, batches + batches, algs)
+    rng = np.random.default_rng(5)
+    for j, b in enumerate(batches):
+        idx = np.sort(rng.choice(b.batch, min(3, b.batch), replace=False))
+        sub = I.Batch(b.family, b.n, b.params[:, idx], b.u0[:, idx])
+        o = oracle_solve(sub, LS)
+        ref = O.polish_batch(b.family, sub.params, o["u"])
+        for (u, st, it, s), tol in ((res[j], 1e-9), (res[len(batches) + j], 1e-8)):
+            assert (st == 0).all() and s == b.batch
+            err = np.abs(u[:, idx] - ref).max(axis=0) / np.maximum(1, np.abs(ref).max(axis=0))
+            assert err.max() <= tol
 
 
 @pytest.mark.parametrize("n,alg", [(6, 5), (12, 5), (40, 4), (24, 7)])

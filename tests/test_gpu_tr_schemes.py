@@ -49,7 +49,8 @@ def test_nocedal_wright_parity(solver, tile, n, family, mixed):
     o = oracle_solve(b, TR | NW, maxiters=300)
     # Rosenbrock at n >= 12 leaves most instances at maxiters; which ones is
     # decided by rounding along 300 passes
-    check_parity(b, g, o, mixed, chaotic=(family == I.FAMILY_ROSENBROCK and n >= 12))
+    check_parity(b, g, o, mixed, rule="chaotic" if (family == I.FAMILY_ROSENBROCK and n >= 12)
+                 else "exact", alg=TR | NW, maxiters=300)
 
 
 def test_scheme_changes_the_iteration(solver):

@@ -43,7 +43,8 @@ def test_warp_parity(solver, family, n, alg, mixed):
     o = oracle_solve(b, alg, maxiters=maxiters)
     # plain Newton on Rosenbrock from U[0,1)^n is rounding-chaotic for n >= 13
     chaotic = family == I.FAMILY_ROSENBROCK and alg == NEWTON and n >= 13
-    check_parity(b, g, o, mixed, chaotic=chaotic)
+    check_parity(b, g, o, mixed, rule="chaotic" if chaotic else "exact", alg=alg,
+                 maxiters=maxiters)
     if family == I.FAMILY_ROSENBROCK:
         ok = g["status"] == 0
         np.testing.assert_allclose(g["u"][:, ok], 1.0, atol=1e-9)

@@ -68,5 +68,14 @@ def test_noalloc_rejects_too_many_groups():
     with pytest.raises(nls.NlsError) as e:
         nls.nls_solve_noalloc(0, [big], NEWTON, 1e-10, 50)
     assert e.value.code == nls.NLS_E_UNSUPPORTED
+    # the other algorithms of nls_solve are not run here; unknown ones are invalid
+    for a in (nls.NLS_POLYALG, nls.NLS_POTRA_PTAK, nls.NLS_HALLEY, nls.NLS_BROYDEN,
+              nls.NLS_MOD_BROYDEN):
+        with pytest.raises(nls.NlsError) as e:
+            nls.nls_solve_noalloc(0, [g], a, 1e-10, 50)
+        assert e.value.code == nls.NLS_E_UNSUPPORTED and "only" in str(e.value)
+    with pytest.raises(nls.NlsError) as e:
+        nls.nls_solve_noalloc(0, [g], nls.NLS_MOD_BROYDEN + 1, 1e-10, 50)
+    assert e.value.code == nls.NLS_E_INVALID
     # A = 0, b = 0: u0 = 0 is already a root of every instance
     assert nls.nls_solve_noalloc(0, [g], NEWTON, 1e-10, 50) == [4]
