@@ -1,50 +1,24 @@
-// CTA-tiled solver instantiations (mixed), register tiles R = 4 (n <= 64) and 8 (n <= 128).
-#include "nls_cta.cuh"
+// CTA tiling (one instance per CTA, n <= 128) of Newton, backtracking and the
+// dogleg trust region, mixed precision (FP32 Jacobian and LU): the column-panel solver of nls_panel.cuh,
+// one instantiation unit per family (nls_panel_mixed_*.cu).
 #include "nls_internal.h"
 
 namespace nls {
 
-template <int R, int FAM>
-static cudaError_t launch_cta_mixed(const SolveArgs &a, int grid, cudaStream_t st)
-{
-    k_solve_cta<R, FAM, true><<<grid, CTA_TPB, cta_smem_bytes<true, R>(), st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int R, int FAM>
-static KernelInfo info_cta_mixed()
-{
-    // more than 48 KB of dynamic shared memory needs an opt-in, once per kernel
-    static const cudaError_t attr = cudaFuncSetAttribute(
-        reinterpret_cast<const void *>(&k_solve_cta<R, FAM, true>),
-        cudaFuncAttributeMaxDynamicSharedMemorySize, cta_smem_bytes<true, R>());
-    (void)attr;
-    KernelInfo k;
-    k.launch = &launch_cta_mixed<R, FAM>;
-    k.func = reinterpret_cast<const void *>(&k_solve_cta<R, FAM, true>);
-    k.block = CTA_TPB;
-    k.smem = cta_smem_bytes<true, R>();
-    k.per_cta = 1;
-    return k;
-}
-
-template <int R>
-static KernelInfo cta_by_family_mixed(int family)
-{
-    switch (family) {
-    case FAM_CUBIC: return info_cta_mixed<R, FAM_CUBIC>();
-    case FAM_BRATU: return info_cta_mixed<R, FAM_BRATU>();
-    case FAM_SQUARE: return info_cta_mixed<R, FAM_SQUARE>();
-    case FAM_ROSENBROCK: return info_cta_mixed<R, FAM_ROSENBROCK>();
-    default: return KernelInfo{};
-    }
-}
+KernelInfo panel_kernel_mixed_cubic(int n);
+KernelInfo panel_kernel_mixed_bratu(int n);
+KernelInfo panel_kernel_mixed_square(int n);
+KernelInfo panel_kernel_mixed_rosenbrock(int n);
 
 KernelInfo cta_kernel_mixed(int family, int n)
 {
-    if (n <= 64) return cta_by_family_mixed<4>(family);
-    if (n <= 128) return cta_by_family_mixed<8>(family);
-    return KernelInfo{};
+    switch (family) {
+    case FAM_CUBIC: return panel_kernel_mixed_cubic(n);
+    case FAM_BRATU: return panel_kernel_mixed_bratu(n);
+    case FAM_SQUARE: return panel_kernel_mixed_square(n);
+    case FAM_ROSENBROCK: return panel_kernel_mixed_rosenbrock(n);
+    default: return KernelInfo{};
+    }
 }
 
 } // namespace nls

@@ -32,8 +32,9 @@ KernelInfo warp_kernel(int family, int n, bool mixed, int lanes = 0);
 } // namespace nls
 
 namespace nls {
-// One instance per 256-thread CTA, register tiles of R x R (R = 4: n <= 64,
-// R = 8: n <= 128).
+// One instance per CTA, n <= 128.  Mixed precision: the column-panel solver
+// (nls_panel.cuh, 16 columns of J per warp); FP64: the 256-thread CTA with
+// R x R block-cyclic register tiles (nls_cta.cuh, R = 4: n <= 64, 8: n <= 128).
 KernelInfo cta_kernel(int family, int n, bool mixed);
 } // namespace nls
 

@@ -1,0 +1,8 @@
+// Column-panel CTA solver instantiations: mixed, bratu family, n <= 32, 64, 96, 128.
+#include "nls_panel_kernels.cuh"
+
+namespace nls {
+
+KernelInfo panel_kernel_mixed_bratu(int n) { return panel_info_for<FAM_BRATU, true>(n); }
+
+} // namespace nls

@@ -476,13 +476,43 @@ NLS_DI void thread_lanes(SolveArgs &a)
             }
             first = false;
             bool got = false;
+            // A whole warp taking 32 consecutive instances whose first is even
+            // (every full refill and every static slot; ld even, params 16-byte
+            // aligned) stages them together with 16-byte loads: per step the
+            // warp reads two elements of its 32 instances, lane l the pair of
+            // instances 2 (l % 16), 2 (l % 16) + 1 of element 2 i + l / 16, and
+            // stores the pair into the two owners' shared-memory columns with
+            // one 16-byte store.  Otherwise every lane loads its own instance's
+            // elements (8-byte loads, still coalesced across the warp).
+            const int64_t k0 = __shfl_sync(FULL, cand, 0);
+            const bool vec = __all_sync(FULL, want && cand == k0 + lane) && (k0 % 2 == 0) &&
+                             (a.ld % 2 == 0) && ((reinterpret_cast<uintptr_t>(a.params) & 15) == 0) &&
+                             k0 + THREAD_TPB <= a.batch;
+            if (vec) {
+                const int half = lane >> 4, pair = 2 * (lane & 15);
+#pragma unroll 4
+                for (int e0 = 0; e0 < E; e0 += 2) {
+                    const int e = e0 + half;
+                    if (e < E) {
+                        const double2 v =
+                            __ldg(reinterpret_cast<const double2 *>(a.params + (int64_t)e * a.ld + k0 + pair));
+                        *reinterpret_cast<double2 *>(sd + e * THREAD_TPB + pair) = v;
+                        if constexpr (MIXED)
+                            *reinterpret_cast<float2 *>(sf + e * THREAD_TPB + pair) =
+                                make_float2(float(v.x), float(v.y));
+                    }
+                }
+                __syncwarp();
+            }
             if (want && cand < a.batch) {
                 k = cand;
+                if (!vec) {
 #pragma unroll 4
-                for (int e = 0; e < E; ++e) {
-                    const double v = __ldg(a.params + (int64_t)e * a.ld + k);
-                    sd[e * THREAD_TPB + lane] = v;
-                    if constexpr (MIXED) sf[e * THREAD_TPB + lane] = float(v);
+                    for (int e = 0; e < E; ++e) {
+                        const double v = __ldg(a.params + (int64_t)e * a.ld + k);
+                        sd[e * THREAD_TPB + lane] = v;
+                        if constexpr (MIXED) sf[e * THREAD_TPB + lane] = float(v);
+                    }
                 }
                 s.init(pv, a, k);
                 got = true;
