@@ -215,6 +215,21 @@ int nls_solve_host(nls_handle h, int family, const double *params, double *u, in
                    int64_t batch, int alg, double abstol, int maxiters, const nls_outputs *out,
                    int64_t *solved);
 
+/* Asynchronous form of nls_solve_host: enqueues the uploads, the solve and
+ * the downloads on the handle's streams and returns at once with a request
+ * id in *req; nls_status(h, *req, ...) waits for it (the results are then in
+ * the host buffers and *solved counts the NLS_SUCCESS instances).  params,
+ * u and the host outputs must stay valid, and must not be written, until
+ * nls_status has returned NLS_OK for the id.  Requests made one after
+ * another run as a pipeline: the next request's uploads overlap the current
+ * request's solve, its solve the current request's downloads.  Each request
+ * in flight holds its own library-owned staging block (about the size of its
+ * device state); blocks are reused by later requests.  Same arguments and
+ * errors as nls_solve_host (plus NLS_E_INVALID for req == NULL). */
+int nls_solve_host_async(nls_handle h, int family, const double *params, double *u, int n,
+                         int64_t batch, int alg, double abstol, int maxiters,
+                         const nls_outputs *out, int64_t *req);
+
 /* Destroy the context; waits for its outstanding work first. */
 int nls_batch_destroy(nls_handle h);
 

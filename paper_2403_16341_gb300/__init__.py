@@ -43,6 +43,7 @@ NLS_OPT_PERSISTENT, NLS_OPT_REFILL_BELOW, NLS_OPT_CTAS_PER_SM, NLS_OPT_GRAPH = 1
 NLS_OPT_DEADLINE_US = 5
 
 EXPORTED = ("nls_batch_create", "nls_solve", "nls_flush", "nls_status", "nls_solve_host",
+            "nls_solve_host_async",
             "nls_batch_destroy", "nls_last_error", "nls_launch_count", "nls_set_option",
             "nls_solve_noalloc", "nls_autotune", "nls_tune_save", "nls_tune_load",
             "nls_server_create", "nls_server_submit", "nls_server_wait", "nls_server_wait_timed",
@@ -100,6 +101,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "nls_status": ([vp, i64, ctypes.POINTER(i64), i32], i32),
             "nls_solve_host": ([vp, i32, vp, vp, i32, i64, i32, dbl, i32, out_p,
                                 ctypes.POINTER(i64)], i32),
+            "nls_solve_host_async": ([vp, i32, vp, vp, i32, i64, i32, dbl, i32, out_p,
+                                      ctypes.POINTER(i64)], i32),
             "nls_batch_destroy": ([vp], i32),
             "nls_last_error": ([vp], ctypes.c_char_p),
             "nls_launch_count": ([vp], i64),
@@ -187,6 +190,18 @@ def nls_solve_host(h, family, params, u, n, batch, alg, abstol, maxiters, status
     _check(h, load_library().nls_solve_host(h, family, params or None, u or None, n, batch, alg,
                                             abstol, maxiters, ctypes.byref(out), ctypes.byref(s)))
     return s.value
+
+
+def nls_solve_host_async(h, family, params, u, n, batch, alg, abstol, maxiters, status=0, iters=0,
+                         resid_inf=0, nfev=0, ngrad=0) -> int:
+    """Enqueue a solve on raw HOST addresses; returns the request id for
+    nls_status (the host buffers must stay untouched until then)."""
+    req = ctypes.c_int64()
+    out = _outs(status, iters, resid_inf, nfev, ngrad)
+    _check(h, load_library().nls_solve_host_async(h, family, params or None, u or None, n, batch,
+                                                  alg, abstol, maxiters, ctypes.byref(out),
+                                                  ctypes.byref(req)))
+    return req.value
 
 
 def nls_batch_destroy(h) -> None:

@@ -71,6 +71,16 @@ struct Tuned {
 };
 constexpr int REFILL_STATIC = -2;
 
+// A request on host buffers (nls_solve_host_async): its chunk requests, its
+// staging block, and its events (the last one follows its copies back).
+struct HostReq {
+    std::vector<int64_t> chunks;
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    std::vector<cudaEvent_t> evs;
+    cudaEvent_t done = nullptr;
+};
+
 inline long long tune_key(int family, int n, int alg)
 {
     return ((long long)family << 40) | ((long long)n << 24) | (long long)(alg & (NLS_ALG_MASK | NLS_MIXED));
@@ -94,18 +104,19 @@ struct nls_batch {
     unsigned long long *h_ctr = nullptr; // pinned mirror
     std::vector<int64_t> owner;          // ring slot -> request id (0 = free)
     int ring_pos = 0;
-    // staging for nls_solve_host
-    void *d_stage = nullptr;
-    size_t stage_bytes = 0;
+    // nls_solve_host / nls_solve_host_async: staging blocks not in use (by
+    // size), events not in use, and the requests in flight
+    std::multimap<size_t, void *> stage_free;
+    std::vector<cudaEvent_t> ev_free;
+    std::map<int64_t, HostReq> hreqs;
     // cached executable graphs by request-shape signature
     std::map<std::string, cudaGraphExec_t> graphs;
     std::map<const void *, int> occ_cache;
     std::map<long long, Tuned> tuned;
     double *d_tune = nullptr; // autotuner scratch for a prefix of u
     size_t tune_bytes = 0;
-    // nls_solve_host's copy streams (created on first use) and chunk events
+    // the host entry points' copy streams (created on first use)
     cudaStream_t s_in = nullptr, s_out = nullptr;
-    std::vector<cudaEvent_t> host_ev;
 };
 
 static std::mutex g_err_mu;
@@ -744,9 +755,12 @@ int nls_flush(nls_handle h)
     return flush_pending(h);
 }
 
+static int host_status(nls_handle h, int64_t req, int64_t *solved, int timeout_ms);
+
 int nls_status(nls_handle h, int64_t req, int64_t *solved, int timeout_ms)
 {
     if (!h) return NLS_E_INVALID;
+    if (h->hreqs.count(req)) return host_status(h, req, solved, timeout_ms);
     auto it = h->reqs.find(req);
     if (it == h->reqs.end()) return fail(h, NLS_E_NOTFOUND, "unknown request %lld", (long long)req);
     NLS_CUDA(h, cudaSetDevice(h->device));
@@ -771,29 +785,80 @@ int nls_status(nls_handle h, int64_t req, int64_t *solved, int timeout_ms)
     return NLS_OK;
 }
 
-int nls_solve_host(nls_handle h, int family, const double *params, double *u, int n, int64_t batch, int alg,
-                   double abstol, int maxiters, const nls_outputs *out, int64_t *solved)
+// Staging block of at least `need` bytes: the smallest idle block that is
+// not more than twice as large, else a new one (idle blocks are released
+// first when the memory cap would be exceeded).
+static int take_stage(nls_batch *h, size_t need, void **p, size_t *bytes)
+{
+    auto it = h->stage_free.lower_bound(need);
+    if (it != h->stage_free.end() && it->first <= 2 * need) {
+        *p = it->second;
+        *bytes = it->first;
+        h->stage_free.erase(it);
+        return NLS_OK;
+    }
+    if (h->mem_cap && h->mem_used + need > h->mem_cap) {
+        for (auto &kv : h->stage_free) {
+            cudaFree(kv.second);
+            h->mem_used -= kv.first;
+        }
+        h->stage_free.clear();
+    }
+    int rc = dev_alloc(h, p, need);
+    if (rc) return rc;
+    *bytes = need;
+    return NLS_OK;
+}
+
+static int take_event(nls_batch *h, cudaEvent_t *e)
+{
+    if (!h->ev_free.empty()) {
+        *e = h->ev_free.back();
+        h->ev_free.pop_back();
+        return NLS_OK;
+    }
+    NLS_CUDA(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    return NLS_OK;
+}
+
+// Completion of a host request: its copies back are done (which follow every
+// chunk's solve), then the chunks' solved counts; the staging block and the
+// events go back to the handle's pools.
+static int host_status(nls_handle h, int64_t req, int64_t *solved, int timeout_ms)
+{
+    NLS_CUDA(h, cudaSetDevice(h->device));
+    HostReq &q = h->hreqs[req];
+    int rc = wait_event(h, q.done, timeout_ms);
+    if (rc) return rc;
+    int64_t total = 0;
+    for (int64_t c : q.chunks) {
+        int64_t sv = 0;
+        rc = nls_status(h, c, &sv, -1);
+        if (rc) return rc;
+        total += sv;
+    }
+    h->stage_free.emplace(q.stage_bytes, q.stage);
+    for (cudaEvent_t e : q.evs) h->ev_free.push_back(e);
+    h->hreqs.erase(req);
+    if (solved) *solved = total;
+    return NLS_OK;
+}
+
+int nls_solve_host_async(nls_handle h, int family, const double *params, double *u, int n, int64_t batch,
+                         int alg, double abstol, int maxiters, const nls_outputs *out, int64_t *req)
 {
     int rc = validate(h, family, params, u, n, batch, alg, abstol, maxiters);
     if (rc) return rc;
+    if (!req) return fail(h, NLS_E_INVALID, "req is NULL");
     NLS_CUDA(h, cudaSetDevice(h->device));
     const size_t E = (size_t)n_params(family, n);
     const size_t bp = E * (size_t)batch * 8, bu = (size_t)n * (size_t)batch * 8, bo = (size_t)batch * 4;
     const size_t need = bp + bu + 4 * bo + (size_t)batch * 8 + 5 * 256;
-    if (need > h->stage_bytes) {
-        if (h->d_stage) {
-            NLS_CUDA(h, cudaStreamSynchronize(h->stream));
-            cudaFree(h->d_stage);
-            h->mem_used -= h->stage_bytes;
-            h->d_stage = nullptr;
-            h->stage_bytes = 0;
-        }
-        rc = dev_alloc(h, &h->d_stage, need);
-        if (rc) return rc;
-        h->stage_bytes = need;
-    }
+    HostReq q;
+    rc = take_stage(h, need, &q.stage, &q.stage_bytes);
+    if (rc) return rc;
     auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
-    char *base = static_cast<char *>(h->d_stage);
+    char *base = static_cast<char *>(q.stage);
     double *dp = reinterpret_cast<double *>(base);
     double *du = reinterpret_cast<double *>(base + align(bp));
     double *dres = reinterpret_cast<double *>(base + align(bp) + align(bu));
@@ -805,70 +870,95 @@ int nls_solve_host(nls_handle h, int family, const double *params, double *u, in
     // go up on s_in while chunk c is solved on the handle's stream, and the
     // results of finished chunks come back on s_out; events order the three.
     // Chunks address the staging arrays with leading dimension `batch`.  The
-    // poly-algorithm gathers whole arrays, so it keeps one chunk.
-    // chunks of at least 2^17 instances (several waves of a persistent grid),
-    // at most eight: the first upload and the last download stay exposed
+    // poly-algorithm gathers whole arrays, so it keeps one chunk.  Chunks of at
+    // least 2^17 instances (several waves of a persistent grid), at most
+    // eight.  Requests made one after another queue on the same three streams,
+    // so a request's uploads overlap the previous request's solves.
     const int64_t C = (alg & NLS_ALG_MASK) == NLS_POLYALG ? 1 : std::min<int64_t>(8, std::max<int64_t>(1, batch >> 17));
     if (C > 1) {
         if (!h->s_in) NLS_CUDA(h, cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking));
         if (!h->s_out) NLS_CUDA(h, cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking));
-        while ((int64_t)h->host_ev.size() < 2 * C) {
-            cudaEvent_t e;
-            NLS_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-            h->host_ev.push_back(e);
-        }
     }
+    auto give_back = [&]() {
+        h->stage_free.emplace(q.stage_bytes, q.stage);
+        for (cudaEvent_t e : q.evs) h->ev_free.push_back(e);
+    };
+    const int nev = C > 1 ? (int)(2 * C) + 1 : 1;
+    for (int i = 0; i < nev; ++i) {
+        cudaEvent_t e;
+        rc = take_event(h, &e);
+        if (rc) {
+            give_back();
+            return rc;
+        }
+        q.evs.push_back(e);
+    }
+    q.done = q.evs.back();
     cudaStream_t sin = C > 1 ? h->s_in : h->stream, sout = C > 1 ? h->s_out : h->stream;
-    std::vector<int64_t> reqs;
+#define NLS_HCUDA(call)                                                                                \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            give_back();                                                                               \
+            return fail(h, NLS_E_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));              \
+        }                                                                                              \
+    } while (0)
     for (int64_t c = 0; c < C; ++c) {
         const int64_t k0 = batch * c / C, kc = batch * (c + 1) / C - k0;
         if (bp)
-            NLS_CUDA(h, cudaMemcpy2DAsync(dp + k0, batch * 8, params + k0, batch * 8, kc * 8, E,
-                                          cudaMemcpyHostToDevice, sin));
+            NLS_HCUDA(cudaMemcpy2DAsync(dp + k0, batch * 8, params + k0, batch * 8, kc * 8, E,
+                                        cudaMemcpyHostToDevice, sin));
         if (bu)
-            NLS_CUDA(h, cudaMemcpy2DAsync(du + k0, batch * 8, u + k0, batch * 8, kc * 8, n, cudaMemcpyHostToDevice,
-                                          sin));
+            NLS_HCUDA(cudaMemcpy2DAsync(du + k0, batch * 8, u + k0, batch * 8, kc * 8, n, cudaMemcpyHostToDevice,
+                                        sin));
         if (C > 1) {
-            NLS_CUDA(h, cudaEventRecord(h->host_ev[2 * c], sin));
-            NLS_CUDA(h, cudaStreamWaitEvent(h->stream, h->host_ev[2 * c], 0));
+            NLS_HCUDA(cudaEventRecord(q.evs[2 * c], sin));
+            NLS_HCUDA(cudaStreamWaitEvent(h->stream, q.evs[2 * c], 0));
         }
         nls_outputs dout{out && out->status ? dst + k0 : nullptr, out && out->iters ? dit + k0 : nullptr,
                          out && out->resid_inf ? dres + k0 : nullptr, out && out->nfev ? dnf + k0 : nullptr,
                          out && out->ngrad ? dng + k0 : nullptr};
-        int64_t req = 0;
-        rc = enqueue(h, family, bp ? dp + k0 : nullptr, du + k0, n, kc, batch, alg, abstol, maxiters, &dout, &req);
-        if (rc) return rc;
-        reqs.push_back(req);
-        rc = flush_pending(h);
-        if (rc) return rc;
+        int64_t creq = 0;
+        rc = enqueue(h, family, bp ? dp + k0 : nullptr, du + k0, n, kc, batch, alg, abstol, maxiters, &dout, &creq);
+        if (rc == NLS_OK) rc = flush_pending(h);
+        if (rc) {
+            give_back();
+            return rc;
+        }
+        q.chunks.push_back(creq);
         if (C > 1) {
-            NLS_CUDA(h, cudaEventRecord(h->host_ev[2 * c + 1], h->stream));
-            NLS_CUDA(h, cudaStreamWaitEvent(sout, h->host_ev[2 * c + 1], 0));
+            NLS_HCUDA(cudaEventRecord(q.evs[2 * c + 1], h->stream));
+            NLS_HCUDA(cudaStreamWaitEvent(sout, q.evs[2 * c + 1], 0));
         }
         if (bu)
-            NLS_CUDA(h, cudaMemcpy2DAsync(u + k0, batch * 8, du + k0, batch * 8, kc * 8, n, cudaMemcpyDeviceToHost,
-                                          sout));
+            NLS_HCUDA(cudaMemcpy2DAsync(u + k0, batch * 8, du + k0, batch * 8, kc * 8, n, cudaMemcpyDeviceToHost,
+                                        sout));
         if (out && out->status)
-            NLS_CUDA(h, cudaMemcpyAsync(out->status + k0, dst + k0, kc * 4, cudaMemcpyDeviceToHost, sout));
+            NLS_HCUDA(cudaMemcpyAsync(out->status + k0, dst + k0, kc * 4, cudaMemcpyDeviceToHost, sout));
         if (out && out->iters)
-            NLS_CUDA(h, cudaMemcpyAsync(out->iters + k0, dit + k0, kc * 4, cudaMemcpyDeviceToHost, sout));
+            NLS_HCUDA(cudaMemcpyAsync(out->iters + k0, dit + k0, kc * 4, cudaMemcpyDeviceToHost, sout));
         if (out && out->nfev)
-            NLS_CUDA(h, cudaMemcpyAsync(out->nfev + k0, dnf + k0, kc * 4, cudaMemcpyDeviceToHost, sout));
+            NLS_HCUDA(cudaMemcpyAsync(out->nfev + k0, dnf + k0, kc * 4, cudaMemcpyDeviceToHost, sout));
         if (out && out->ngrad)
-            NLS_CUDA(h, cudaMemcpyAsync(out->ngrad + k0, dng + k0, kc * 4, cudaMemcpyDeviceToHost, sout));
+            NLS_HCUDA(cudaMemcpyAsync(out->ngrad + k0, dng + k0, kc * 4, cudaMemcpyDeviceToHost, sout));
         if (out && out->resid_inf)
-            NLS_CUDA(h, cudaMemcpyAsync(out->resid_inf + k0, dres + k0, kc * 8, cudaMemcpyDeviceToHost, sout));
+            NLS_HCUDA(cudaMemcpyAsync(out->resid_inf + k0, dres + k0, kc * 8, cudaMemcpyDeviceToHost, sout));
     }
-    NLS_CUDA(h, cudaStreamSynchronize(sout));
-    int64_t total = 0;
-    for (int64_t req : reqs) {
-        int64_t sv = 0;
-        rc = nls_status(h, req, &sv, -1);
-        if (rc) return rc;
-        total += sv;
-    }
-    if (solved) *solved = total;
+    NLS_HCUDA(cudaEventRecord(q.done, sout));
+#undef NLS_HCUDA
+    const int64_t id = h->next_id++;
+    h->hreqs[id] = std::move(q);
+    *req = id;
     return NLS_OK;
+}
+
+int nls_solve_host(nls_handle h, int family, const double *params, double *u, int n, int64_t batch, int alg,
+                   double abstol, int maxiters, const nls_outputs *out, int64_t *solved)
+{
+    int64_t req = 0;
+    int rc = nls_solve_host_async(h, family, params, u, n, batch, alg, abstol, maxiters, out, &req);
+    if (rc) return rc;
+    return nls_status(h, req, solved, -1);
 }
 
 int nls_batch_destroy(nls_handle h)
@@ -877,15 +967,22 @@ int nls_batch_destroy(nls_handle h)
     cudaSetDevice(h->device);
     flush_pending(h);
     cudaStreamSynchronize(h->stream);
+    if (h->s_in) cudaStreamSynchronize(h->s_in);
+    if (h->s_out) cudaStreamSynchronize(h->s_out);
     for (auto &kv : h->reqs)
         if (kv.second.poly_ws) cudaFree(kv.second.poly_ws);
     h->reqs.clear();
+    for (auto &kv : h->hreqs) {
+        if (kv.second.stage) cudaFree(kv.second.stage);
+        for (cudaEvent_t e : kv.second.evs) cudaEventDestroy(e);
+    }
+    h->hreqs.clear();
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     if (h->d_tune) cudaFree(h->d_tune);
-    if (h->d_stage) cudaFree(h->d_stage);
+    for (auto &kv : h->stage_free) cudaFree(kv.second);
     if (h->d_ctr) cudaFree(h->d_ctr);
     if (h->h_ctr) cudaFreeHost(h->h_ctr);
-    for (cudaEvent_t e : h->host_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->ev_free) cudaEventDestroy(e);
     if (h->s_in) cudaStreamDestroy(h->s_in);
     if (h->s_out) cudaStreamDestroy(h->s_out);
     delete h;

@@ -12,8 +12,8 @@
 //  * Warp p factors its panel alone.  For each column the pivot is the
 //    first position holding the largest |a_ik| over the remaining rows: each
 //    lane forms (|a| + 1, ~position) keys for its rows, three warp reductions
-//    give the largest key and the row holding it.  The owner lane publishes
-//    the pivot row through a small shared-memory buffer, every lane scales
+//    give the largest key and the row holding it.  The pivot row's entries
+//    reach every lane by select + shuffle from its owner, every lane scales
 //    its rows' entries of the column into multipliers (published to shared
 //    memory for the other warps) and updates the panel's remaining columns
 //    and the right-hand side (forward substitution).  The rows' positions
@@ -56,7 +56,6 @@ struct PanelSmem {
     P L[2][NM][C + 1];  // a panel's multipliers by row, buffer p & 1 (padded: conflict-free)
     P part[NW][NM];     // per-warp partial row sums of J g
     alignas(16) P W[NW][C][C + 4]; // per warp: the panel's pivot rows in its columns, then U12 (rows 16-byte aligned)
-    alignas(16) P prow[NW][C]; // per warp: the current pivot row of its panel
     int piv[NM];        // row at position k (after the LU: the pivot row of step k)
     int rpos[NM];       // position of row r
     double rd[3][NW];
@@ -264,6 +263,14 @@ struct PanelSolver {
         for (int s = 1; s < S; ++s) x = (slot == s) ? v[s] : x;
         return x;
     }
+    // Entry (r, cc) of this warp's columns on every lane, r = 32 slot + src.
+    NLS_DI static P prow_entry(const P (&a)[S][C], int cc, int slot, int src)
+    {
+        P colv[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) colv[s] = a[s][cc];
+        return __shfl_sync(0xffffffffu, pick(colv, slot), src);
+    }
     // Row r's component of a per-row vector held as y[s] for rows lane + 32 s.
     NLS_DI static P vec_value(const P (&y)[S], int r)
     {
@@ -273,12 +280,10 @@ struct PanelSolver {
     // Warp `warp` factors its panel (the columns it owns) and carries the
     // right-hand side sm.y along; returns false on a zero or non-finite pivot
     // (uniform over the warp).  The positions of the lane's rows are kept in
-    // registers (pos) and published to sm.rpos by their owners; the pivot row
-    // reaches the warp through the warp's own row buffer in shared memory.
+    // registers (pos) and published to sm.rpos by their owners.
     NLS_DI bool factor_panel(P (&a)[S][C], uint32_t &rem, SM &sm, int buf) const
     {
         const K inf = inf_bits(P(0));
-        P *prbuf = sm.prow[warp];
         P yv[S];
         int pos[S];
 #pragma unroll
@@ -313,23 +318,10 @@ struct PanelSolver {
             K kmax;
             warp_pivot_row(key[0], brow, kmax, pmin, prow);
             const int src = prow & 31, pslot = prow >> 5;
-            // the owner publishes the pivot row's columns c .. C-1 (16-byte chunks)
-            if (lane == src) {
-                switch (pslot) {
-#define NLS_PANEL_SLOT(SS)                                                                       \
-    case SS:                                                                                     \
-        if constexpr (SS < S) {                                                                  \
-            _Pragma("unroll") for (int cc = 0; cc < C; ++cc) if (cc >= (c & ~(16 / (int)sizeof(P) - 1))) \
-                prbuf[cc] = a[SS < S ? SS : 0][cc];                                              \
-        }                                                                                        \
-        break;
-                    NLS_PANEL_SLOT(0) NLS_PANEL_SLOT(1) NLS_PANEL_SLOT(2) NLS_PANEL_SLOT(3)
-#undef NLS_PANEL_SLOT
-                }
-            }
-            __syncwarp();
+            // the pivot row's entries reach every lane by select + shuffle, each
+            // just before it is used (no branch, no copy of the row held)
             if (kmax <= K(1) || kmax - K(1) >= inf) ok = false;
-            const P r = pivot_rcp(prbuf[c]);
+            const P r = pivot_rcp(prow_entry(a, c, pslot, src));
             // the pivot row leaves the remaining set; positions: it takes kk,
             // the row that held kk takes the pivot's old position
 #pragma unroll
@@ -360,7 +352,7 @@ struct PanelSolver {
 #pragma unroll
             for (int cc = 0; cc < C; ++cc) {
                 if (cc <= c) continue;
-                const P v = prbuf[cc];
+                const P v = prow_entry(a, cc, pslot, src);
 #pragma unroll
                 for (int s = 0; s < S; ++s)
                     if ((rem >> s) & 1u) a[s][cc] -= l[s] * v;
@@ -373,7 +365,6 @@ struct PanelSolver {
                 sm.rdiag[kk] = r;
                 sm.piv[kk] = prow;
             }
-            __syncwarp(); // the row buffer is rewritten at the next step
         }
 #pragma unroll
         for (int s = 0; s < S; ++s)

@@ -182,6 +182,47 @@ def test_host_entry_point_matches_device(solver, case):
     np.testing.assert_array_equal(nf, g["nfev"])
 
 
+def test_host_async_requests_pipeline(solver):
+    # several host requests in flight at once (pinned buffers, chunked and
+    # not, different algorithms and families): each equals the device-buffer
+    # path, whatever order they are waited for in; a poll before completion
+    # may time out, and a finished id is released
+    import ctypes
+    import torch
+    import paper_2403_16341_gb300 as nls
+    cases = [(I.cubic_batch(8, 300001, config_id=1, b_half_width=5.0), TR | MIXED),
+             (I.cubic_batch(8, 300001, config_id=1, b_half_width=5.0), LS),
+             (I.bratu_batch(12, 5001, config_id=2), LS | MIXED),
+             (I.cubic_batch(3, 1024, config_id=0), NEWTON)]
+    ptr = lambda t: t.data_ptr() if t.numel() else 0
+    held, reqs = [], []
+    for b, alg in cases:
+        p = torch.from_numpy(np.ascontiguousarray(b.params)).pin_memory()
+        u = torch.from_numpy(np.ascontiguousarray(b.u0)).pin_memory()
+        st = torch.zeros(b.batch, dtype=torch.int32).pin_memory()
+        it = torch.zeros(b.batch, dtype=torch.int32).pin_memory()
+        rs = torch.zeros(b.batch, dtype=torch.float64).pin_memory()
+        held.append((p, u, st, it, rs))
+        reqs.append(nls.nls_solve_host_async(solver.h, b.family, ptr(p), ptr(u), b.n, b.batch, alg,
+                                             1e-10, 50, ptr(st), ptr(it), ptr(rs)))
+    # a poll: None while in flight; once it reports completion the id is released
+    first = nls.nls_status(solver.h, reqs[0], 0)
+    assert first is None or first >= 0
+    polled = {0: first} if first is not None else {}
+    for i in (3, 1, 0, 2):
+        (b, alg), (p, u, st, it, rs) = cases[i], held[i]
+        solved = polled[i] if i in polled else nls.nls_status(solver.h, reqs[i])
+        g = gpu_solve(solver, b, alg)
+        assert solved == g["solved"]
+        np.testing.assert_array_equal(u.numpy(), g["u"])
+        np.testing.assert_array_equal(st.numpy(), g["status"])
+        np.testing.assert_array_equal(it.numpy(), g["iters"])
+        np.testing.assert_array_equal(rs.numpy(), g["resid"])
+        with pytest.raises(nls.NlsError) as e:
+            nls.nls_status(solver.h, reqs[i])
+        assert e.value.code == nls.NLS_E_NOTFOUND
+
+
 def test_grouped_requests(solver):
     # several requests flushed together complete independently and equal solo runs
     import torch
