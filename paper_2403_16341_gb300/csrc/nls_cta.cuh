@@ -11,11 +11,14 @@
 // LU with partial pivoting (Sec. 3.2), rows never move: every row carries
 // the position it would have after the interchanges, and the pivot at step
 // k is the first position >= k holding the largest |a_ik| (the choice an
-// explicit-swap LU makes).  Step k: the 16 owners of column k post their
-// best candidate; after a barrier every thread reduces the 16 candidates,
-// the owners write the multipliers, the owners of the pivot row write it;
-// after a second barrier all threads update their tiles.  The right-hand
+// explicit-swap LU makes).  Step k: the 16 owners of column k (one
+// half-warp) reduce their candidates, write the multipliers and publish the
+// pivot; after the step's one barrier every thread takes the pivot row's
+// entries of its columns by shuffles and updates its tile.  The right-hand
 // side is eliminated alongside; back substitution walks the positions down.
+// This tiling serves the FP64 Newton-family solves (mixed precision takes the
+// column-panel kernel of nls_panel.cuh), and the NEXT-4 solvers and the
+// adjoint in both precisions.
 //
 // The Jacobian tile comes from forward-mode duals over the stencil of each
 // owned row (Sec. 2.4).  The globalisations are those of the other tilings.
