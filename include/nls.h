@@ -332,7 +332,9 @@ typedef struct nls_server_timing {
     double t_launch;   /* its wave's copies and solve were enqueued          */
     double t_done;     /* the dispatcher saw its results in host memory      */
     float h2d_ms;      /* device time of its wave's host-to-device copies    */
-    float solve_ms;    /* device time of its wave's solve (one flush)        */
+    float solve_ms;    /* from the end of those copies to the end of its
+                          wave's flush on the stream: the host's enqueue of
+                          the wave's requests, then the solve              */
     float d2h_ms;      /* from the end of that solve to its results copied   */
     int wave_requests; /* requests in its wave                               */
 } nls_server_timing;

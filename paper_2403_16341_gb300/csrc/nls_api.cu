@@ -361,14 +361,18 @@ static int launch_graph(nls_batch *h, const std::vector<Request *> &rs, const st
         cudaGraphNode_t node = nullptr;
         NLS_CUDA(h, cudaGraphAddKernelNode(&node, g, &ms, 1, &kp));
         kn.push_back(node);
-        sig << r.kern.func << ';'; // grids may differ: cudaGraphExecUpdate takes them
         ++launched;
     }
     cudaGraphNode_t cp = nullptr;
     NLS_CUDA(h, cudaGraphAddMemcpyNode1D(&cp, g, kn.empty() ? &ms : kn.data(), kn.empty() ? 1 : kn.size(),
                                          h->h_ctr + s0, h->d_ctr + s0, sizeof(unsigned long long) * nctr,
                                          cudaMemcpyDeviceToHost));
-    sig << '#' << nctr;
+    // The cache key is the graph's shape only: cudaGraphExecUpdate takes a
+    // kernel node's new function, grid and arguments, so every flush with the
+    // same number of kernels reuses one executable graph.  (Keyed by the
+    // kernel list, a server's waves of mixed requests would instantiate a new
+    // graph for most waves, at a few hundred microseconds each.)
+    sig << launched << '#' << nctr;
     const std::string key = sig.str();
     auto it = h->graphs.find(key);
     cudaGraphExec_t exec = nullptr;

@@ -44,6 +44,7 @@ struct CtaSmem {
     P red[CTA_T][CTA_NMAX]; // partial sums of J^T F and J g
     int pos_row[CTA_NMAX];  // row holding pivot position k
     int row_pos[CTA_NMAX];  // position of row i after the interchanges so far
+    int qidx[CTA_NMAX];     // compaction after block b: 16 b + pair index of a moving row
     uint64_t ckey[2];       // pivot of step k in slot k & 1: key, position, row
     int cpos[2], crow[2];
     double rd[3][CTA_TPB / 32];
@@ -65,6 +66,9 @@ struct CtaSolver {
     using K = decltype(mag_bits(P(0)));
     static constexpr int NM = CTA_T * R;
     using SM = CtaSmemU<MIXED, NM>;
+    // the LU's compaction stages 32 rows in the space of U (unused until the
+    // factorisation ends)
+    static_assert(NM * (NM + 1) >= 2 * CTA_T * NM, "compaction buffer");
 
     int tid, ty, tx, lane, warp, n;
     int64_t B, k;
@@ -78,6 +82,14 @@ struct CtaSolver {
 
     NLS_DI int row(int a) const { return ty + CTA_T * a; }
     NLS_DI int col(int b) const { return tx + CTA_T * b; }
+    // bit a: row(a) < n
+    NLS_DI uint32_t exist_mask() const
+    {
+        uint32_t m = 0;
+#pragma unroll
+        for (int a = 0; a < R; ++a) m |= (row(a) < n ? 1u : 0u) << a;
+        return m;
+    }
 
     // ------------------------------------------------------------ reductions
     // K block sums with one pair of barriers (warps summed in a fixed order,
@@ -231,21 +243,23 @@ struct CtaSolver {
     // non-finite pivot (uniform over the CTA).  The 16 owners of column k are
     // one half-warp (tx = tid / 16), so the pivot candidates are reduced with
     // shuffles; every thread then reads the single winner.
+    template <bool COMPACT = true>
     NLS_DI bool lu_solve(P (&a)[R][R], SM &sm) const
     {
         const K inf = inf_bits(P(0));
         // bit aa: row(aa) exists and is not a pivot row yet
-        uint32_t remmask = 0;
-#pragma unroll
-        for (int aa = 0; aa < R; ++aa) remmask |= (row(aa) < n ? 1u : 0u) << aa;
+        uint32_t remmask = exist_mask();
         if (tid < n) {
             sm.row_pos[tid] = tid; // position of row tid
             sm.pos_row[tid] = tid; // row at position tid
+            if (COMPACT) sm.qidx[tid] = -1;
         }
         __syncthreads();
         bool ok = true;
 #pragma unroll
         for (int b = 0; b < R; ++b) {
+            // slots below lo hold pivot rows only (after the compaction below)
+            const int lo = COMPACT ? b : 0;
             for (int c = 0; c < CTA_T; ++c) {
                 const int kk = CTA_T * b + c;
                 if (kk >= n) break;
@@ -257,7 +271,7 @@ struct CtaSolver {
                     int bpos = INT_MAX, brow = -1;
                     P bval = P(0);
 #pragma unroll
-                    for (int aa = 0; aa < R; ++aa) {
+                    for (int aa = lo; aa < R; ++aa) {
                         if (!((remmask >> aa) & 1u)) continue;
                         const int i = row(aa);
                         const int pi = sm.row_pos[i];
@@ -303,7 +317,7 @@ struct CtaSolver {
                     const P r = rcp(pv);
                     // ... which then write the multipliers of their rows and the pivot
 #pragma unroll
-                    for (int aa = 0; aa < R; ++aa) {
+                    for (int aa = lo; aa < R; ++aa) {
                         const int i = row(aa);
                         const bool elim = ((remmask >> aa) & 1u) && i != prow_i;
                         const P l = a[aa][b] * r;
@@ -342,8 +356,8 @@ struct CtaSolver {
                 switch (ap) {
 #define NLS_PROW_CASE(A)                                                                          \
     case A:                                                                                       \
-        if (A < R) {                                                                              \
-            _Pragma("unroll") for (int bb = b; bb < R; ++bb) pr[bb] =                             \
+        if (A < R && A >= lo) {                                                                   \
+            _Pragma("unroll") for (int bb = b; bb < R; ++bb) if (!COMPACT || CTA_T * bb < n) pr[bb] = \
                 __shfl_sync(0xffffffffu, a[A < R ? A : 0][bb], tp, CTA_T);                        \
         }                                                                                         \
         break;
@@ -353,16 +367,80 @@ struct CtaSolver {
                 }
                 remmask = rem;
 #pragma unroll
-                for (int aa = 0; aa < R; ++aa) {
+                for (int aa = lo; aa < R; ++aa) {
                     if (!((rem >> aa) & 1u)) continue;
                     const P l = sm.lcol[par][row(aa)];
 #pragma unroll
                     for (int bb = b; bb < R; ++bb) {
+                        if (COMPACT && CTA_T * bb >= n) break; // CTA-uniform: no columns left
                         if (bb > b || tx > c) a[aa][bb] -= l * pr[bb];
                     }
                 }
-                if (tid < n && tid != prow_i) sm.rhs[tid] -= sm.lcol[par][tid] * sm.rhs[prow_i];
+                if (tid < n && tid >= CTA_T * lo && tid != prow_i)
+                    sm.rhs[tid] -= sm.lcol[par][tid] * sm.rhs[prow_i];
                 // the next barrier orders these reads before buffer `par` is reused
+            }
+            // Compaction, which leaves every result unchanged (a row carries its
+            // position, multipliers and right-hand side): after the 16 steps of
+            // block b, the block's pivot rows that sit outside slot b trade
+            // places with the rows of slot b that are not pivots, so that slot b
+            // holds exactly the block's pivot rows and the later steps skip it
+            // as a whole.  The row update work drops from all R slots per step to
+            // the R - b live ones.
+            if (COMPACT && b + 1 < R && CTA_T * (b + 1) < n) {
+                __syncthreads(); // the block's last update and bookkeeping are done
+                if (warp == 0) {
+                    // lanes 0..15: the pivot row of position 16 b + j; lanes 16..31:
+                    // row 16 b + j of slot b.  The q-th mover of each half pairs up
+                    // with the q-th mover of the other.
+                    const int j = lane & (CTA_T - 1);
+                    const bool outer = lane < CTA_T;
+                    const int r = outer ? sm.pos_row[CTA_T * b + j] : CTA_T * b + j;
+                    const bool mv = outer ? (r / CTA_T != b) : (sm.row_pos[r] >= CTA_T * (b + 1));
+                    const unsigned bal = __ballot_sync(0xffffffffu, mv);
+                    const unsigned mine = outer ? (bal & 0xFFFFu) : (bal >> CTA_T);
+                    const int q = __popc(mine & ((1u << j) - 1u));
+                    if (mv) {
+                        sm.qidx[r] = CTA_T * b + q;
+                        if (outer) {
+                            unsigned o = bal >> CTA_T;
+                            for (int t = 0; t < q; ++t) o &= o - 1u;
+                            const int ra = CTA_T * b + __ffs(o) - 1; // its partner in slot b
+                            const int pb = CTA_T * b + j;             // position of row r
+                            const int pa = sm.row_pos[ra];
+                            const P hb = sm.rhs[r], ha = sm.rhs[ra];
+                            sm.row_pos[ra] = pb;
+                            sm.pos_row[pb] = ra;
+                            sm.rhs[ra] = hb;
+                            sm.row_pos[r] = pa;
+                            sm.pos_row[pa] = r;
+                            sm.rhs[r] = ha;
+                        }
+                    }
+                }
+                __syncthreads();
+                // rows of slot b to stage rows 0..15, the pivot rows to 16..31
+                P *stage = &sm.U[0][0];
+#pragma unroll
+                for (int aa = b; aa < R; ++aa) {
+                    const int qv = row(aa) < n ? sm.qidx[row(aa)] : -1;
+                    if ((qv >> 4) == b) {
+                        P *st = stage + ((aa == b ? 0 : CTA_T) + (qv & (CTA_T - 1))) * NM;
+#pragma unroll
+                        for (int bb = 0; bb < R; ++bb) st[col(bb)] = a[aa][bb];
+                    }
+                }
+                __syncthreads();
+#pragma unroll
+                for (int aa = b; aa < R; ++aa) {
+                    const int qv = row(aa) < n ? sm.qidx[row(aa)] : -1;
+                    if ((qv >> 4) == b) {
+                        const P *st = stage + ((aa == b ? CTA_T : 0) + (qv & (CTA_T - 1))) * NM;
+#pragma unroll
+                        for (int bb = 0; bb < R; ++bb) a[aa][bb] = st[col(bb)];
+                    }
+                }
+                remmask = exist_mask() & ~((2u << b) - 1u);
             }
         }
         __syncthreads();

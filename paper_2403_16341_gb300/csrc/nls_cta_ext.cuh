@@ -208,7 +208,9 @@ struct CtaSolverBroyden : CtaSolverExtBase<R, FAM, MIXED> {
                 this->jacobian_tile(a, sm);
                 if (own) sm.rhs[t] = P(0);
                 __syncthreads();
-                if (!this->lu_solve(a, sm)) {
+                // one factorisation per instance: the LU without row compaction
+                // (which would only add registers here)
+                if (!this->template lu_solve<false>(a, sm)) {
                     status = ST_SINGULAR;
                     return;
                 }

@@ -235,6 +235,8 @@ static void dispatcher(nls_server *s)
             nls_handle h = s->workers[w];
             cudaStream_t st = s->streams[w];
             auto W = std::make_shared<WaveEvents>();
+            // all of the wave's input copies first, back to back on the stream;
+            // then the requests are enqueued (host work only until the flush)
             if (W->ok) cudaEventRecord(W->a, st);
             for (auto &t : wave[w]) {
                 const size_t E = n_params(t->family, t->n);
@@ -243,16 +245,23 @@ static void dispatcher(nls_server *s)
                 if (E && t->batch) e = cudaMemcpyAsync(L.p, t->h_params, E * t->batch * 8, cudaMemcpyHostToDevice, st);
                 if (e == cudaSuccess && t->batch)
                     e = cudaMemcpyAsync(L.u, t->h_u, size_t(t->n) * t->batch * 8, cudaMemcpyHostToDevice, st);
-                nls_outputs dout{L.status, L.iters, L.resid, L.nfev, L.ngrad};
-                int rc = e == cudaSuccess ? nls_solve(h, t->family, E ? L.p : nullptr, L.u, t->n, t->batch, t->alg,
-                                                      t->abstol, t->maxiters, &dout, &t->req)
-                                          : NLS_E_CUDA;
-                if (rc) {
+                if (e != cudaSuccess) {
                     t->failed = true;
-                    t->err = e != cudaSuccess ? cudaGetErrorString(e) : nls_last_error(h);
+                    t->err = cudaGetErrorString(e);
                 }
             }
             if (W->ok) cudaEventRecord(W->b, st);
+            for (auto &t : wave[w]) {
+                if (t->failed) continue;
+                const size_t E = n_params(t->family, t->n);
+                const Layout L = layout(*t, s->arena_d);
+                nls_outputs dout{L.status, L.iters, L.resid, L.nfev, L.ngrad};
+                if (nls_solve(h, t->family, E ? L.p : nullptr, L.u, t->n, t->batch, t->alg, t->abstol, t->maxiters,
+                              &dout, &t->req)) {
+                    t->failed = true;
+                    t->err = nls_last_error(h);
+                }
+            }
             nls_flush(h);
             if (W->ok) cudaEventRecord(W->c, st);
             const double t_launch = s->now();
