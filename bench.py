@@ -353,6 +353,19 @@ def _serve_pass(nls, local, payloads, pinned, alg, rate, warm_s, meas_s, pool, s
     stages["stream_wait_and_notice"] = np.array([t["t_done"] - t["t_launch"] for t in tm]) * 1e3 - dev
     worst = int(lat.argmax())
     wreq = payloads[meas[worst] % pool]
+    # who the tail is: requests above the p99 latency against all requests,
+    # by the bytes their inputs move to the device and the share of their
+    # latency spent in the wave's input copies
+    in_mb = np.array([(payloads[i % pool].params.size + payloads[i % pool].u0.size) * 8 / 1e6
+                      for i in meas])
+    p99 = float(np.percentile(lat, 99))
+    over = lat > p99
+    tail = {"p99_ms": p99, "requests_over_p99": int(over.sum()),
+            "input_mb_median_all": float(np.median(in_mb)),
+            "input_mb_median_over_p99": float(np.median(in_mb[over])) if over.any() else None,
+            "h2d_share_over_p99": float(np.median(stages["h2d"][over] / lat[over])) if over.any() else None,
+            "p99_ms_inputs_below_1mb": float(np.percentile(lat[in_mb < 1.0], 99)) if (in_mb < 1.0).any() else None,
+            "frac_requests_inputs_below_1mb": float((in_mb < 1.0).mean())}
     breakdown = {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99)),
                      "max": float(v.max())} for k, v in stages.items()}
     return {"workload": "Poisson arrivals at 2000 req/s, 1-4096 instances per request "
@@ -367,7 +380,7 @@ def _serve_pass(nls, local, payloads, pinned, alg, rate, warm_s, meas_s, pool, s
             "max_ms": float(lat.max()), "frac_over_1ms": float((lat > 1.0).mean()),
             "p99_submit_lag_ms": float(np.percentile(lag, 99)),
             "worst_at_s": float(arrivals[meas[worst]]),
-            "stages_ms": breakdown,
+            "stages_ms": breakdown, "tail": tail,
             "worst_request": {"latency_ms": float(lat[worst]), "n": wreq.n, "batch": wreq.batch,
                               "family": wreq.family, "wave_requests": tm[worst]["wave_requests"],
                               **{k: float(v[worst]) for k, v in stages.items()}}}

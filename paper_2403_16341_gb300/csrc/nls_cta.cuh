@@ -12,10 +12,13 @@
 // the position it would have after the interchanges, and the pivot at step
 // k is the first position >= k holding the largest |a_ik| (the choice an
 // explicit-swap LU makes).  Step k: the 16 owners of column k (one
-// half-warp) reduce their candidates, write the multipliers and publish the
-// pivot; after the step's one barrier every thread takes the pivot row's
-// entries of its columns by shuffles and updates its tile.  The right-hand
-// side is eliminated alongside; back substitution walks the positions down.
+// half-warp) reduce their candidates (redux.sync on 32-bit halves of the
+// keys), write the multipliers and publish the pivot; after the step's one
+// barrier every thread takes the pivot row's entries of its columns by
+// shuffles and updates its tile.  After each block of 16 steps the block's
+// pivot rows are compacted into one tile slot, which the later steps skip.
+// The right-hand side is eliminated alongside; back substitution walks the
+// positions down.
 // This tiling serves the FP64 Newton-family solves (mixed precision takes the
 // column-panel kernel of nls_panel.cuh), and the NEXT-4 solvers and the
 // adjoint in both precisions.
@@ -284,31 +287,29 @@ struct CtaSolver {
                             bval = a[aa][b];
                         }
                     }
-                    // ... reduced over the half-warp ...
+                    // ... reduced over the half-warp with redux.sync on 32-bit
+                    // halves (largest high word, then the largest low word
+                    // among its holders, then the lowest position among the
+                    // holders of the largest key): one exact 64-bit argmax
                     const unsigned hm = 0xFFFFu << (16 * (c & 1));
                     uint64_t kmax;
                     int pmin;
                     if constexpr (sizeof(K) == 4) {
                         // 32-bit magnitudes: (|a| + 1, complement of the position) in
-                        // one key, so a single max gives the pivot and its position
-                        uint64_t key = brow >= 0 ? ((best + 1) << 32) | (uint32_t)~(uint32_t)bpos : 0;
-#pragma unroll
-                        for (int o = 8; o > 0; o >>= 1) {
-                            const uint64_t w = __shfl_xor_sync(hm, key, o);
-                            key = w > key ? w : key;
-                        }
-                        kmax = key >> 32;
-                        pmin = key ? (int)~(uint32_t)(key & 0xFFFFFFFFu) : INT_MAX;
+                        // one key, so its maximum gives the pivot and its position
+                        const uint32_t kh = brow >= 0 ? (uint32_t)best + 1u : 0u;
+                        const uint32_t kl = brow >= 0 ? ~(uint32_t)bpos : 0u;
+                        const uint32_t H = __reduce_max_sync(hm, kh);
+                        const uint32_t L = __reduce_max_sync(hm, kh == H ? kl : 0u);
+                        kmax = H;
+                        pmin = H ? (int)~L : INT_MAX;
                     } else {
-                        kmax = brow >= 0 ? best + 1 : 0; // +1: a valid zero key beats no candidate
-#pragma unroll
-                        for (int o = 8; o > 0; o >>= 1) {
-                            const uint64_t w = __shfl_xor_sync(hm, kmax, o);
-                            kmax = w > kmax ? w : kmax;
-                        }
-                        pmin = (brow >= 0 && best + 1 == kmax) ? bpos : INT_MAX;
-#pragma unroll
-                        for (int o = 8; o > 0; o >>= 1) pmin = min(pmin, __shfl_xor_sync(hm, pmin, o));
+                        const uint64_t key = brow >= 0 ? best + 1 : 0; // +1: a valid zero key beats no candidate
+                        const uint32_t kh = (uint32_t)(key >> 32), kl = (uint32_t)key;
+                        const uint32_t H = __reduce_max_sync(hm, kh);
+                        const uint32_t L = __reduce_max_sync(hm, kh == H ? kl : 0u);
+                        kmax = ((uint64_t)H << 32) | L;
+                        pmin = __reduce_min_sync(hm, (brow >= 0 && key == kmax) ? bpos : INT_MAX);
                     }
                     const unsigned wb = __ballot_sync(hm, brow >= 0 && bpos == pmin);
                     const int src = wb ? __ffs(wb) - 1 : (16 * (c & 1));
