@@ -209,8 +209,12 @@ int nls_status(nls_handle h, int64_t req, int64_t *solved, int timeout_ms);
  * copies u and the per-instance outputs (HOST pointers in `out`, each may be
  * NULL) back, and waits.  Batches of 2^18 instances and more (not
  * NLS_POLYALG) are pipelined in up to eight chunks: a chunk's upload, solve
- * and download overlap the neighbouring chunks'.  Same arguments and errors as nls_solve, plus
- * NLS_E_NOMEM when the staging buffers would exceed the memory cap. */
+ * and download overlap the neighbouring chunks', and consecutive chunks'
+ * solves run on two alternating streams of the handle, so one chunk's
+ * launch fills the SMs the previous chunk's grid frees as it drains.
+ * Requests made earlier with nls_solve and not yet launched are launched
+ * first, on the handle's stream.  Same arguments and errors as nls_solve,
+ * plus NLS_E_NOMEM when the staging buffers would exceed the memory cap. */
 int nls_solve_host(nls_handle h, int family, const double *params, double *u, int n,
                    int64_t batch, int alg, double abstol, int maxiters, const nls_outputs *out,
                    int64_t *solved);

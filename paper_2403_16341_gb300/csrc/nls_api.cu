@@ -115,9 +115,15 @@ struct nls_batch {
     std::map<long long, Tuned> tuned;
     double *d_tune = nullptr; // autotuner scratch for a prefix of u
     size_t tune_bytes = 0;
-    // the host entry points' copy streams (created on first use)
-    cudaStream_t s_in = nullptr, s_out = nullptr;
+    // the host entry points' copy streams and second solve stream (created on
+    // first use), and the stream flushes launch on while a host request's
+    // chunks alternate between the handle's stream and s_alt (null: the
+    // handle's stream)
+    cudaStream_t s_in = nullptr, s_out = nullptr, s_alt = nullptr;
+    cudaStream_t ls = nullptr;
 };
+
+static cudaStream_t launch_stream(const nls_batch *h) { return h->ls ? h->ls : h->stream; }
 
 static std::mutex g_err_mu;
 static std::string g_err;
@@ -372,7 +378,7 @@ static int launch_graph(nls_batch *h, const std::vector<Request *> &rs, const st
     // same number of kernels reuses one executable graph.  (Keyed by the
     // kernel list, a server's waves of mixed requests would instantiate a new
     // graph for most waves, at a few hundred microseconds each.)
-    sig << launched << '#' << nctr;
+    sig << launched << '#' << nctr << '@' << (const void *)launch_stream(h);
     const std::string key = sig.str();
     auto it = h->graphs.find(key);
     cudaGraphExec_t exec = nullptr;
@@ -394,7 +400,7 @@ static int launch_graph(nls_batch *h, const std::vector<Request *> &rs, const st
         NLS_CUDA(h, cudaGraphInstantiate(&exec, g, 0));
         h->graphs[key] = exec;
     }
-    NLS_CUDA(h, cudaGraphLaunch(exec, h->stream));
+    NLS_CUDA(h, cudaGraphLaunch(exec, launch_stream(h)));
     h->launches += launched;
     return NLS_OK;
 }
@@ -402,15 +408,16 @@ static int launch_graph(nls_batch *h, const std::vector<Request *> &rs, const st
 static int launch_direct(nls_batch *h, const std::vector<Request *> &rs, const std::vector<int> &grids, int s0,
                          int nctr)
 {
-    NLS_CUDA(h, cudaMemsetAsync(h->d_ctr + s0, 0, sizeof(unsigned long long) * nctr, h->stream));
+    const cudaStream_t st = launch_stream(h);
+    NLS_CUDA(h, cudaMemsetAsync(h->d_ctr + s0, 0, sizeof(unsigned long long) * nctr, st));
     for (size_t i = 0; i < rs.size(); ++i) {
         if (!grids[i]) continue;
-        cudaError_t e = rs[i]->kern.launch(rs[i]->args, grids[i], h->stream);
+        cudaError_t e = rs[i]->kern.launch(rs[i]->args, grids[i], st);
         if (e != cudaSuccess) return fail(h, NLS_E_CUDA, "kernel launch: %s", cudaGetErrorString(e));
         ++h->launches;
     }
     NLS_CUDA(h, cudaMemcpyAsync(h->h_ctr + s0, h->d_ctr + s0, sizeof(unsigned long long) * nctr,
-                                cudaMemcpyDeviceToHost, h->stream));
+                                cudaMemcpyDeviceToHost, st));
     return NLS_OK;
 }
 
@@ -468,7 +475,7 @@ static int launch_poly(nls_batch *h, Request &r)
     const bool mixed = (r.alg_flags & NLS_MIXED) != 0;
     PolyWs w;
     poly_layout(B, n, E, static_cast<char *>(r.poly_ws), &w);
-    cudaStream_t st = h->stream;
+    cudaStream_t st = launch_stream(h);
     SolveArgs a = r.args;
     if (!a.status) a.status = w.fst;
     if (!a.iters) a.iters = w.fit;
@@ -579,8 +586,8 @@ static int flush_pending(nls_batch *h)
         }
     if (any_poly)
         NLS_CUDA(h, cudaMemcpyAsync(h->h_ctr + s0, h->d_ctr + s0, sizeof(unsigned long long) * 2 * nreq,
-                                    cudaMemcpyDeviceToHost, h->stream));
-    NLS_CUDA(h, cudaEventRecord(*ev, h->stream));
+                                    cudaMemcpyDeviceToHost, launch_stream(h)));
+    NLS_CUDA(h, cudaEventRecord(*ev, launch_stream(h)));
     h->pending.clear();
     return NLS_OK;
 }
@@ -855,6 +862,10 @@ int nls_solve_host_async(nls_handle h, int family, const double *params, double 
     if (rc) return rc;
     if (!req) return fail(h, NLS_E_INVALID, "req is NULL");
     NLS_CUDA(h, cudaSetDevice(h->device));
+    // requests made with nls_solve before this call launch on the handle's
+    // stream, in its order, before any chunk takes the second solve stream
+    rc = flush_pending(h);
+    if (rc) return rc;
     const size_t E = (size_t)n_params(family, n);
     const size_t bp = E * (size_t)batch * 8, bu = (size_t)n * (size_t)batch * 8, bo = (size_t)batch * 4;
     const size_t need = bp + bu + 4 * bo + (size_t)batch * 8 + 5 * 256;
@@ -871,17 +882,21 @@ int nls_solve_host_async(nls_handle h, int family, const double *params, double 
     int32_t *dnf = dit + align(bo) / 4;
     int32_t *dng = dnf + align(bo) / 4;
     // Large batches are pipelined in chunks of instances: chunk c + 1's inputs
-    // go up on s_in while chunk c is solved on the handle's stream, and the
-    // results of finished chunks come back on s_out; events order the three.
-    // Chunks address the staging arrays with leading dimension `batch`.  The
-    // poly-algorithm gathers whole arrays, so it keeps one chunk.  Chunks of at
-    // least 2^17 instances (several waves of a persistent grid), at most
-    // eight.  Requests made one after another queue on the same three streams,
-    // so a request's uploads overlap the previous request's solves.
+    // go up on s_in while chunk c is solved, and the results of finished
+    // chunks come back on s_out; events order the streams.  The chunks' solves
+    // alternate between the handle's stream and s_alt, so a chunk's launch can
+    // take the SMs its predecessor's persistent grid frees while that grid
+    // drains (its tail), instead of every chunk paying its own.  Chunks address
+    // the staging arrays with leading dimension `batch`.  The poly-algorithm
+    // gathers whole arrays, so it keeps one chunk.  Chunks of at least 2^17
+    // instances (several waves of a persistent grid), at most eight.  Requests
+    // made one after another queue on the same streams, so a request's
+    // uploads overlap the previous request's solves.
     const int64_t C = (alg & NLS_ALG_MASK) == NLS_POLYALG ? 1 : std::min<int64_t>(8, std::max<int64_t>(1, batch >> 17));
     if (C > 1) {
         if (!h->s_in) NLS_CUDA(h, cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking));
         if (!h->s_out) NLS_CUDA(h, cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking));
+        if (!h->s_alt) NLS_CUDA(h, cudaStreamCreateWithFlags(&h->s_alt, cudaStreamNonBlocking));
     }
     auto give_back = [&]() {
         h->stage_free.emplace(q.stage_bytes, q.stage);
@@ -915,23 +930,28 @@ int nls_solve_host_async(nls_handle h, int family, const double *params, double 
         if (bu)
             NLS_HCUDA(cudaMemcpy2DAsync(du + k0, batch * 8, u + k0, batch * 8, kc * 8, n, cudaMemcpyHostToDevice,
                                         sin));
+        const cudaStream_t ss = (C > 1 && (c & 1)) ? h->s_alt : h->stream; // this chunk's solve
         if (C > 1) {
             NLS_HCUDA(cudaEventRecord(q.evs[2 * c], sin));
-            NLS_HCUDA(cudaStreamWaitEvent(h->stream, q.evs[2 * c], 0));
+            NLS_HCUDA(cudaStreamWaitEvent(ss, q.evs[2 * c], 0));
         }
         nls_outputs dout{out && out->status ? dst + k0 : nullptr, out && out->iters ? dit + k0 : nullptr,
                          out && out->resid_inf ? dres + k0 : nullptr, out && out->nfev ? dnf + k0 : nullptr,
                          out && out->ngrad ? dng + k0 : nullptr};
         int64_t creq = 0;
         rc = enqueue(h, family, bp ? dp + k0 : nullptr, du + k0, n, kc, batch, alg, abstol, maxiters, &dout, &creq);
-        if (rc == NLS_OK) rc = flush_pending(h);
+        if (rc == NLS_OK) {
+            h->ls = ss;
+            rc = flush_pending(h);
+            h->ls = nullptr;
+        }
         if (rc) {
             give_back();
             return rc;
         }
         q.chunks.push_back(creq);
         if (C > 1) {
-            NLS_HCUDA(cudaEventRecord(q.evs[2 * c + 1], h->stream));
+            NLS_HCUDA(cudaEventRecord(q.evs[2 * c + 1], ss));
             NLS_HCUDA(cudaStreamWaitEvent(sout, q.evs[2 * c + 1], 0));
         }
         if (bu)
@@ -973,6 +993,7 @@ int nls_batch_destroy(nls_handle h)
     cudaStreamSynchronize(h->stream);
     if (h->s_in) cudaStreamSynchronize(h->s_in);
     if (h->s_out) cudaStreamSynchronize(h->s_out);
+    if (h->s_alt) cudaStreamSynchronize(h->s_alt);
     for (auto &kv : h->reqs)
         if (kv.second.poly_ws) cudaFree(kv.second.poly_ws);
     h->reqs.clear();
@@ -989,6 +1010,7 @@ int nls_batch_destroy(nls_handle h)
     for (cudaEvent_t e : h->ev_free) cudaEventDestroy(e);
     if (h->s_in) cudaStreamDestroy(h->s_in);
     if (h->s_out) cudaStreamDestroy(h->s_out);
+    if (h->s_alt) cudaStreamDestroy(h->s_alt);
     delete h;
     return NLS_OK;
 }

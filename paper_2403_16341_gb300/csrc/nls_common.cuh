@@ -215,13 +215,15 @@ struct Family<FAM_CUBIC, N> {
         if constexpr (J == N) return acc;
         else return dot<I, J + 1>(p, u, acc + p.template get<T>(I * N + J) * u.template get<J>());
     }
+    // The sum starts from A_i0 u_0 - b_i, so every term of the row is one
+    // fused multiply-add: N + 1 FP64 FMAs and one multiply per row.
     template <int I, class PV, class U>
     NLS_DI static auto row(const PV &p, const U &u)
     {
         using T = typename U::scalar;
-        auto s = dot<I, 1>(p, u, p.template get<T>(I * N) * u.template get<0>());
+        auto s = dot<I, 1>(p, u, p.template get<T>(I * N) * u.template get<0>() - p.template get<T>(N * N + I));
         auto ui = u.template get<I>();
-        return s + ui * ui * ui - p.template get<T>(N * N + I);
+        return s + ui * ui * ui;
     }
     template <class T, class PV>
     NLS_DI static void jac_analytic(const PV &p, const T (&u)[N], T (&J)[N][N])
