@@ -222,8 +222,7 @@ struct Family<FAM_CUBIC, N> {
     {
         using T = typename U::scalar;
         auto s = dot<I, 1>(p, u, p.template get<T>(I * N) * u.template get<0>() - p.template get<T>(N * N + I));
-        auto ui = u.template get<I>();
-        return s + ui * ui * ui;
+        return s + cube(u.template get<I>());
     }
     template <class T, class PV>
     NLS_DI static void jac_analytic(const PV &p, const T (&u)[N], T (&J)[N][N])

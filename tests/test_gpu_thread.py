@@ -182,6 +182,36 @@ def test_host_entry_point_matches_device(solver, case):
     np.testing.assert_array_equal(nf, g["nfev"])
 
 
+def test_pending_device_request_then_chunked_host_request(solver):
+    # a device-buffer request made with nls_solve and not yet flushed is
+    # launched on the handle's stream before a host request's chunks, which
+    # alternate between two solve streams; both equal their requests made
+    # alone
+    import torch
+    import paper_2403_16341_gb300 as nls
+    bd = I.cubic_batch(8, 70001, config_id=1, b_half_width=5.0)
+    bh = I.cubic_batch(8, 300001, config_id=2, b_half_width=5.0)  # two chunks
+    ref_d, ref_h = gpu_solve(solver, bd, LS | MIXED), gpu_solve(solver, bh, TR)
+    dev = torch.device("cuda", 0)
+    p = torch.from_numpy(np.ascontiguousarray(bd.params)).to(dev)
+    u = torch.from_numpy(np.ascontiguousarray(bd.u0)).to(dev)
+    st = torch.empty(bd.batch, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    rd = solver.submit(bd.family, p, u, LS | MIXED, outputs=(st, None, None, None))
+    hp = torch.from_numpy(np.ascontiguousarray(bh.params)).pin_memory()
+    hu = torch.from_numpy(np.ascontiguousarray(bh.u0)).pin_memory()
+    hst = torch.zeros(bh.batch, dtype=torch.int32).pin_memory()
+    rh = nls.nls_solve_host_async(solver.h, bh.family, hp.data_ptr(), hu.data_ptr(), bh.n, bh.batch, TR,
+                                  1e-10, 50, hst.data_ptr())
+    assert nls.nls_status(solver.h, rh) == ref_h["solved"]
+    assert solver.wait(rd) == ref_d["solved"]
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(hu.numpy(), ref_h["u"])
+    np.testing.assert_array_equal(hst.numpy(), ref_h["status"])
+    np.testing.assert_array_equal(u.cpu().numpy(), ref_d["u"])
+    np.testing.assert_array_equal(st.cpu().numpy(), ref_d["status"])
+
+
 def test_host_async_requests_pipeline(solver):
     # several host requests in flight at once (pinned buffers, chunked and
     # not, different algorithms and families): each equals the device-buffer
