@@ -43,6 +43,7 @@ ABSTOL = 1e-10
 MAXITERS = 50
 NEWTON, LS, TR = 0, 1, 2
 MIXED = 1 << 8
+REFINE = 1 << 14  # FP32 LU with classical iterative refinement of each Newton step
 VARIANTS = [("newton_backtrack_fp64", LS), ("newton_backtrack_mixed", LS | MIXED),
             ("trust_dogleg_fp64", TR), ("trust_dogleg_mixed", TR | MIXED)]
 WORKLOAD = "cubic n=8, 2^20 instances, NR+backtracking and TR-dogleg x {FP64, mixed}"
@@ -676,14 +677,19 @@ def config2_uneven(torch, nls, local, dev, stream, steps, warmup, modes=True):
 
 def config4_bratu_large(torch, solver, dev, stream, steps, warmup):
     """16,384 Bratu instances, n uniform in 64..128, trust-region dogleg, one
-    CTA per instance: the FP32 LU with FP64 residual against the FP64 LU."""
+    CTA per instance: the FP32 LU with FP64 residual (Newton's own correction
+    of the FP32 steps), the same with classical iterative refinement of every
+    Newton step (two passes of r = -F - J dN in FP64), and the FP64 LU."""
     dbs = _device_batches(torch, I.workload_bratu_large(), dev)
     res = {"config": ("16,384 Bratu instances, n uniform in 64..128, lambda ~ U[0.5, 3], "
                       "trust-region dogleg, one CTA per instance")}
     with ClockSampler(dev.index or 0) as clk:
-        for name, alg in (("fp32_lu_fp64_residual", TR | MIXED), ("fp64_lu", TR)):
+        for name, alg in (("fp32_lu_fp64_residual", TR | MIXED), ("fp32_lu_refined", TR | MIXED | REFINE),
+                          ("fp64_lu", TR)):
             ms, sv, nl = time_flush(torch, solver, dbs, alg, steps, max(warmup, 3), stream)
-            res[name] = {"ms": ms, "solved_per_s": sv / (ms / 1e3), "solved": sv, "launches": nl}
+            passes = sum(int(outs[1].sum().item()) for *_, outs in dbs) / sum(b.batch for b, *_ in dbs)
+            res[name] = {"ms": ms, "solved_per_s": sv / (ms / 1e3), "solved": sv, "launches": nl,
+                         "mean_passes": passes}
             res[name]["max_rel_err"] = sampled_error(dbs, alg, 1)
     res["clocks"] = clk.summary()
     return res

@@ -92,7 +92,7 @@ enum nls_flags {
     NLS_TILE_THREAD = 1 << 10, /* force one instance per thread   (n <= 8)      */
     NLS_TILE_WARP = 1 << 11,   /* force one instance per warp     (n <= 32)     */
     NLS_TILE_CTA = 1 << 12,    /* force one instance per CTA      (n <= 128)    */
-    NLS_TR_NOCEDAL_WRIGHT = 1 << 13 /* trust-region radius update of Tab. 3's
+    NLS_TR_NOCEDAL_WRIGHT = 1 << 13, /* trust-region radius update of Tab. 3's
                                   NocedalWright scheme (Nocedal & Wright,
                                   Algorithm 4.1): shrink x1/4 iff rho < 1/4,
                                   double (cap 1e3) iff rho > 3/4 and the step
@@ -101,6 +101,18 @@ enum nls_flags {
                                   double iff rho > 3/4, shrink x1/4 on
                                   rejection.  Valid with NLS_TRUST_DOGLEG and
                                   NLS_POLYALG (its trust-region stage).      */
+    NLS_REFINE = 1 << 14       /* with NLS_MIXED: classical iterative
+                                  refinement of every Newton step (the second
+                                  reading of "FP32 LU with FP64 residual
+                                  refinement" for n up to 128): after the
+                                  FP32 LU gives dN, two passes of
+                                  r = -F - J dN with J in FP64 (evaluated on
+                                  the fly, no FP64 copy of J is stored) and
+                                  dN += the FP32 factors' solve of r.  Runs
+                                  on the CTA tiling (any n <= 128) with
+                                  NLS_NEWTON, NLS_NEWTON_BACKTRACK and
+                                  NLS_TRUST_DOGLEG; other combinations, and
+                                  nls_autotune, return NLS_E_UNSUPPORTED.   */
 };
 
 /* Per-instance outcome. */

@@ -32,6 +32,7 @@ NLS_TILE_THREAD = 1 << 10
 NLS_TILE_WARP = 1 << 11
 NLS_TILE_CTA = 1 << 12
 NLS_TR_NOCEDAL_WRIGHT = 1 << 13
+NLS_REFINE = 1 << 14
 # nls_inst_status
 (NLS_SUCCESS, NLS_MAXITERS, NLS_SINGULAR, NLS_NONFINITE, NLS_LS_FAILED, NLS_TR_STALLED,
  NLS_ABORTED) = range(7)

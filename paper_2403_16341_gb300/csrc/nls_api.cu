@@ -215,6 +215,8 @@ static int select_kernel(nls_batch *h, int family, int n, int alg, KernelInfo *o
         } else {
             *out = nls::cta_ext_kernel(family, n, a, mixed);
         }
+    } else if (alg & NLS_REFINE) {
+        tiles = NLS_TILE_CTA; // the refined solve is built on the CTA tiling only
     } else {
         if (!tiles) tiles = n <= 8 ? NLS_TILE_THREAD : n <= 32 ? NLS_TILE_WARP : NLS_TILE_CTA;
     }
@@ -604,8 +606,12 @@ static int validate(nls_batch *h, int family, const double *params, const double
     const int a = alg & NLS_ALG_MASK;
     if (a > NLS_MOD_BROYDEN) return fail(h, NLS_E_INVALID, "unknown algorithm %d", a);
     if (alg & ~(NLS_ALG_MASK | NLS_MIXED | NLS_ANALYTIC_JAC | NLS_TILE_THREAD | NLS_TILE_WARP | NLS_TILE_CTA |
-                NLS_TR_NOCEDAL_WRIGHT))
+                NLS_TR_NOCEDAL_WRIGHT | NLS_REFINE))
         return fail(h, NLS_E_INVALID, "unknown flags in alg 0x%x", alg);
+    if ((alg & NLS_REFINE) && (!(alg & NLS_MIXED) || a > NLS_TRUST_DOGLEG || (alg & (NLS_TILE_THREAD | NLS_TILE_WARP))))
+        return fail(h, NLS_E_UNSUPPORTED,
+                    "NLS_REFINE refines the FP32 solves of NLS_MIXED Newton, backtracking or trust region on the "
+                    "CTA tiling (alg 0x%x)", alg);
     if ((alg & NLS_TR_NOCEDAL_WRIGHT) && a != NLS_TRUST_DOGLEG && a != NLS_POLYALG)
         return fail(h, NLS_E_INVALID, "NLS_TR_NOCEDAL_WRIGHT needs a trust-region algorithm (alg %d)", a);
     if (batch > 0 && !u) return fail(h, NLS_E_INVALID, "u is NULL");
@@ -726,6 +732,7 @@ static int enqueue(nls_batch *h, int family, const double *params, double *u, in
     r.args.alg = alg & NLS_ALG_MASK;
     r.alg_flags = alg;
     r.args.tr_scheme = (alg & NLS_TR_NOCEDAL_WRIGHT) ? nls::TR_NOCEDAL_WRIGHT : nls::TR_SIMPLE;
+    r.args.refine = (alg & NLS_REFINE) ? 2 : 0;
     r.args.abstol = abstol;
     r.args.maxiters = maxiters;
     r.args.budget_ns = (unsigned long long)h->opt.deadline_us * 1000ull;
@@ -1031,6 +1038,7 @@ int nls_autotune(nls_handle h, int family, const double *params, double *u, int 
     if (rc) return rc;
     if (alg & (NLS_TILE_THREAD | NLS_TILE_WARP | NLS_TILE_CTA))
         return fail(h, NLS_E_INVALID, "nls_autotune chooses the tiling: pass no tiling flag");
+    if (alg & NLS_REFINE) return fail(h, NLS_E_UNSUPPORTED, "NLS_REFINE runs the CTA tiling only: nothing to tune");
     if ((alg & NLS_ALG_MASK) == NLS_POLYALG)
         return fail(h, NLS_E_INVALID, "tune the stage algorithms, not NLS_POLYALG");
     if ((alg & NLS_ALG_MASK) >= NLS_POTRA_PTAK && (alg & NLS_ANALYTIC_JAC))

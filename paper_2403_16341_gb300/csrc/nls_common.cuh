@@ -71,6 +71,9 @@ struct SolveArgs {
     // passed since the kernel started; unfinished instances end NLS_ABORTED
     unsigned long long budget_ns;
     int tr_scheme; // TR_SIMPLE or TR_NOCEDAL_WRIGHT
+    // mixed precision, CTA tiling: iterative-refinement steps per Newton
+    // solve (r = -F - J64 dN in FP64, re-solved with the FP32 factors); 0: none
+    int refine;
 };
 
 // Outcome of one trust-region trial step (Sec. 2.2.2, Eq. 15): returns

@@ -198,6 +198,30 @@ struct PanelSolver {
         }
     }
 
+    // (J(u) v)_t in FP64 at the current iterate sm.u, for t < n (0 beyond):
+    // the FP64 Jacobian row of each family applied to v, evaluated on the fly
+    // (no FP64 copy of J is held).  Iterative refinement's residual.
+    NLS_DI double jdot64_t(const double *v, const SM &sm) const
+    {
+        const int t = tid;
+        if (t >= n) return 0.0;
+        const double ut = sm.u[t];
+        if constexpr (FAM == FAM_CUBIC) {
+            double s = 3.0 * ut * ut * v[t];
+            for (int j = 0; j < n; ++j) s = fma(__ldg(params + (int64_t)(t * n + j) * B + k), v[j], s);
+            return s;
+        } else if constexpr (FAM == FAM_BRATU) {
+            const double inv_h2 = double((n + 1) * (n + 1));
+            const double left = t > 0 ? v[t - 1] : 0.0;
+            const double right = t < n - 1 ? v[t + 1] : 0.0;
+            return inv_h2 * ((left + (-2.0) * v[t]) + right) + lam * exp(ut) * v[t];
+        } else if constexpr (FAM == FAM_SQUARE) {
+            return 2.0 * ut * v[t];
+        } else {
+            return t == 0 ? -v[0] : 10.0 * (v[t] - 2.0 * sm.u[t - 1] * v[t - 1]);
+        }
+    }
+
     // ------------------------------------------------------------ Jacobian
     // this warp's C columns of J for the lane's S rows
     NLS_DI void jacobian_cols(P (&a)[S][C], const SM &sm) const
@@ -430,28 +454,12 @@ struct PanelSolver {
         __syncwarp();
     }
 
-    // Solves J x = rhs (rhs by row in sm.y, x by column to sm.x); false on a
-    // zero or non-finite pivot (uniform over the CTA).
-    NLS_DI bool lu_solve(P (&a)[S][C], SM &sm) const
+    // Back substitution with the factors in a: y (by row, sm.y, already
+    // forward-eliminated) to x (by column, sm.x), column by column from the
+    // last warp's to the first's.
+    NLS_DI void back_sub(const P (&a)[S][C], SM &sm) const
     {
-        uint32_t rem = 0;
-#pragma unroll
-        for (int s = 0; s < S; ++s) rem |= (row(s) < n ? 1u : 0u) << s;
-        if (tid < n) {
-            sm.piv[tid] = tid;
-            sm.rpos[tid] = tid;
-        }
-        if (tid == 0) sm.singular = 0;
-        __syncthreads();
         const int np = (n + C - 1) / C;
-        for (int p = 0; p < np; ++p) {
-            const int buf = p & 1;
-            if (warp == p && !factor_panel(a, rem, sm, buf) && lane == 0) sm.singular = 1;
-            __syncthreads(); // the one barrier of the panel
-            if (sm.singular) return false;
-            if (warp > p) apply_panel(a, rem, sm, p, buf);
-        }
-        // back substitution, column by column from the last warp's to the first's
         int rp[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) rp[s] = row(s) < n ? sm.rpos[row(s)] : INT_MAX;
@@ -476,6 +484,65 @@ struct PanelSolver {
             }
             __syncthreads();
         }
+    }
+
+    // A second right-hand side with the factors of lu_solve (multipliers left
+    // of each row's final position in its column, U from it on; sm.piv,
+    // sm.rpos, sm.rdiag): y (by row, sm.y) to x (by column, sm.x).  The
+    // forward elimination replays the steps in position order, panel by
+    // panel (each warp holds every row of its columns), then the back
+    // substitution.
+    NLS_DI void lu_apply(const P (&a)[S][C], SM &sm) const
+    {
+        const int np = (n + C - 1) / C;
+        int rp[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) rp[s] = row(s) < n ? sm.rpos[row(s)] : INT_MAX;
+        for (int w = 0; w < np; ++w) {
+            if (warp == w) {
+                P yv[S];
+#pragma unroll
+                for (int s = 0; s < S; ++s) yv[s] = row(s) < n ? sm.y[row(s)] : P(0);
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const int kk = col(c);
+                    if (kk >= n) break;
+                    const P yk = vec_value(yv, sm.piv[kk]);
+#pragma unroll
+                    for (int s = 0; s < S; ++s)
+                        if (rp[s] > kk && rp[s] != INT_MAX) yv[s] -= a[s][c] * yk;
+                }
+#pragma unroll
+                for (int s = 0; s < S; ++s)
+                    if (row(s) < n) sm.y[row(s)] = yv[s];
+            }
+            __syncthreads();
+        }
+        back_sub(a, sm);
+    }
+
+    // Solves J x = rhs (rhs by row in sm.y, x by column to sm.x); false on a
+    // zero or non-finite pivot (uniform over the CTA).
+    NLS_DI bool lu_solve(P (&a)[S][C], SM &sm) const
+    {
+        uint32_t rem = 0;
+#pragma unroll
+        for (int s = 0; s < S; ++s) rem |= (row(s) < n ? 1u : 0u) << s;
+        if (tid < n) {
+            sm.piv[tid] = tid;
+            sm.rpos[tid] = tid;
+        }
+        if (tid == 0) sm.singular = 0;
+        __syncthreads();
+        const int np = (n + C - 1) / C;
+        for (int p = 0; p < np; ++p) {
+            const int buf = p & 1;
+            if (warp == p && !factor_panel(a, rem, sm, buf) && lane == 0) sm.singular = 1;
+            __syncthreads(); // the one barrier of the panel
+            if (sm.singular) return false;
+            if (warp > p) apply_panel(a, rem, sm, p, buf);
+        }
+        back_sub(a, sm);
         return true;
     }
 
@@ -555,6 +622,17 @@ struct PanelSolver {
             }
             if (tid < n) sm.dN[tid] = double(sm.x[tid]);
             __syncthreads();
+            // classical iterative refinement of the Newton step: the FP64
+            // residual of J dN = -F, re-solved with the same FP32 factors
+            for (int r = 0; r < A.refine; ++r) {
+                const double res = tid < n ? -sm.F[tid] - jdot64_t(sm.dN, sm) : 0.0;
+                __syncthreads();
+                if (tid < n) sm.y[tid] = P(res);
+                __syncthreads();
+                lu_apply(a, sm);
+                if (tid < n) sm.dN[tid] += double(sm.x[tid]);
+                __syncthreads();
+            }
             need_jac = false;
         }
         const int t = tid;

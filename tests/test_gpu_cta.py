@@ -11,6 +11,7 @@ pytestmark = pytest.mark.gpu
 
 NEWTON, LS, TR = 0, 1, 2
 MIXED, TILE_WARP, TILE_CTA = 1 << 8, 1 << 11, 1 << 12
+REFINE = 1 << 14
 
 
 @pytest.fixture(scope="module")
@@ -79,6 +80,67 @@ def test_bratu_large_full_size_sampled(solver, mixed):
             check_parity(sub, gs, oracle_solve(sub, TR), mixed)
             checked += idx.size
     assert checked >= 40
+
+
+@pytest.mark.parametrize("family", [I.FAMILY_CUBIC, I.FAMILY_BRATU, I.FAMILY_SQUARE,
+                                    I.FAMILY_ROSENBROCK])
+@pytest.mark.parametrize("n", [5, 33, 64, 100, 128])
+@pytest.mark.parametrize("alg", [NEWTON, LS, TR])
+def test_refined_mixed_parity(solver, family, n, alg):
+    # FP32 LU with two steps of classical iterative refinement per Newton
+    # step (r = -F - J dN in FP64, re-solved with the FP32 factors): the
+    # Newton steps are FP64-accurate, so the roots meet the FP64 gate and the
+    # pass counts follow the FP64 oracle's
+    if family == I.FAMILY_ROSENBROCK and n > 16:
+        n = 16  # the Rosenbrock conditioning grows like 2^n
+    b = make(family, n, 61)
+    g = gpu_solve(solver, b, alg | MIXED | REFINE)
+    o = oracle_solve(b, alg)
+    # statuses: every instance the oracle solves is solved (the mixed rule);
+    # Rosenbrock from U[0,1)^n keeps its chaotic rule
+    rule = "chaotic" if family == I.FAMILY_ROSENBROCK else "exact"
+    err = check_parity(b, g, o, mixed=True, rule=rule, alg=alg)
+    both = (g["status"] == 0) & (o["status"] == 0)
+    if family != I.FAMILY_ROSENBROCK:
+        assert err.max() <= FP64_TOL
+        assert (g["iters"][both] == o["iters"][both]).mean() >= 0.95
+
+
+def test_refined_mixed_bratu_large_sampled(solver):
+    # the Bratu n = 64..128 configuration with refinement: every instance
+    # solved, the sampled roots within the FP64 gate, and the mean pass count
+    # of the FP64-LU kernel (the refined steps are FP64-accurate)
+    batches = I.workload_bratu_large()
+    rng = np.random.default_rng(2)
+    checked = 0
+    for b in batches[::4]:
+        g = gpu_solve(solver, b, TR | MIXED | REFINE)
+        g64 = gpu_solve(solver, b, TR)
+        assert g["solved"] == b.batch and (g["resid"] <= 1e-10).all()
+        assert abs(g["iters"].mean() - g64["iters"].mean()) <= 0.05
+        idx = np.sort(rng.choice(b.batch, min(4, b.batch), replace=False))
+        sub = I.Batch(b.family, b.n, b.params[:, idx], b.u0[:, idx])
+        gs = {k: (v[:, idx] if k == "u" else v[idx]) for k, v in g.items() if k != "solved"}
+        gs["solved"] = int((gs["status"] == 0).sum())
+        err = check_parity(sub, gs, oracle_solve(sub, TR), False)
+        assert err.max() <= FP64_TOL
+        checked += idx.size
+    assert checked >= 40
+
+
+def test_refine_flag_combinations(solver):
+    import paper_2403_16341_gb300 as nls
+    import torch
+    b = I.cubic_batch(40, 8, config_id=2)
+    p = torch.from_numpy(np.ascontiguousarray(b.params)).cuda()
+    u = torch.from_numpy(np.ascontiguousarray(b.u0)).cuda()
+    for alg in (LS | REFINE, LS | MIXED | REFINE | TILE_WARP, 4 | MIXED | REFINE, 3 | MIXED | REFINE):
+        with pytest.raises(nls.NlsError) as e:
+            solver.submit(b.family, p, u, alg)
+        assert e.value.code == nls.NLS_E_UNSUPPORTED
+    with pytest.raises(nls.NlsError) as e:
+        solver.autotune(b.family, p, u, LS | MIXED | REFINE)
+    assert e.value.code == nls.NLS_E_UNSUPPORTED
 
 
 def test_cta_singular_nan_and_maxiters(solver):
