@@ -162,6 +162,25 @@ struct mask_of<Dual<M_N, M, T>> {
     static constexpr uint32_t value = M;
 };
 
+constexpr int THREAD_TPB = 32; // one warp per CTA: lanes never wait on each other
+
+template <int N, int FAM, bool MIXED>
+constexpr int thread_smem_bytes()
+{
+    return THREAD_TPB * family_params<FAM>(N) * (8 + (MIXED ? 4 : 0));
+}
+
+// The FP64 Newton-family kernel also keeps the trust region's g = J^T F and
+// J g in the lane's shared-memory columns, after the staged parameters (in
+// mixed precision they are FP32 and stay in registers: their shared copy
+// would cost an eighth CTA per SM).
+template <int N, int FAM, bool MIXED>
+constexpr int thread_newton_smem_bytes()
+{
+    return MIXED ? thread_smem_bytes<N, FAM, MIXED>()
+                 : (thread_smem_bytes<N, FAM, MIXED>() + 15) / 16 * 16 + 2 * N * THREAD_TPB * 8;
+}
+
 template <int N, int FAM, bool MIXED, bool ANALYTIC>
 struct ThreadSolver {
     using P = typename std::conditional<MIXED, float, double>::type;
@@ -211,7 +230,26 @@ struct ThreadSolver {
 
     // ------------------------------------------------------------ lane state
     double u[N], F[N], dN[N];
-    P g[N], Jg[N];
+    // g = J^T F and J g of the trust region.  FP64: element j of the lane's
+    // column in shared memory (out of the register file, which J, u, F and
+    // the Newton step fill); mixed: FP32 registers.
+    P greg_[MIXED ? N : 1], jgreg_[MIXED ? N : 1];
+    NLS_DI static P *gcol()
+    {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        constexpr int off = (thread_smem_bytes<N, FAM, MIXED>() + 15) / 16 * 16;
+        return reinterpret_cast<P *>(smem_raw + off) + threadIdx.x;
+    }
+    NLS_DI P &g(int j)
+    {
+        if constexpr (MIXED) return greg_[j];
+        else return gcol()[j * THREAD_TPB];
+    }
+    NLS_DI P &Jg(int i)
+    {
+        if constexpr (MIXED) return jgreg_[i];
+        else return gcol()[(N + i) * THREAD_TPB];
+    }
     // F and the Newton step in the Jacobian precision; in FP64 mode they are
     // F and dN themselves (no second copy across passes)
     P Fp_[MIXED ? N : 1], dNp_[MIXED ? N : 1];
@@ -270,15 +308,15 @@ struct ThreadSolver {
             P s = P(0);
 #pragma unroll
             for (int i = 0; i < N; ++i) s = fma(J[i][j], Fp(i), s);
-            g[j] = s;
+            g(j) = s;
         }
         if (jg) {
 #pragma unroll
             for (int i = 0; i < N; ++i) {
                 P s = P(0);
 #pragma unroll
-                for (int j = 0; j < N; ++j) s = fma(J[i][j], g[j], s);
-                Jg[i] = s;
+                for (int j = 0; j < N; ++j) s = fma(J[i][j], g(j), s);
+                Jg(i) = s;
             }
         }
     }
@@ -371,26 +409,31 @@ struct ThreadSolver {
                 }
                 P gg = P(0), JgJg = P(0);
 #pragma unroll
-                for (int i = 0; i < N; ++i) { gg = fma(g[i], g[i], gg); JgJg = fma(Jg[i], Jg[i], JgJg); }
+                for (int i = 0; i < N; ++i) {
+                    const P gi = g(i), jgi = Jg(i);
+                    gg = fma(gi, gi, gg);
+                    JgJg = fma(jgi, jgi, JgJg);
+                }
                 const P t = gg / JgJg; // Cauchy point c = -t g minimises m along -g
                 const P cc = t * t * gg;
                 if (cc >= D2) {
                     const P sc = P(Delta) / nls_sqrt(gg);
 #pragma unroll
-                    for (int i = 0; i < N; ++i) d[i] = double(-sc * g[i]);
+                    for (int i = 0; i < N; ++i) d[i] = double(-sc * g(i));
                     pred = double(sc * (P(2) * gg - sc * JgJg)); // J d = -sc J g
                 } else {
                     P w[N], aa = P(0), bb = P(0);
 #pragma unroll
                     for (int i = 0; i < N; ++i) {
-                        w[i] = dNp(i) + t * g[i];
+                        const P gi = g(i);
+                        w[i] = dNp(i) + t * gi;
                         aa = fma(w[i], w[i], aa);
-                        bb = fma(-t * g[i], w[i], bb);
+                        bb = fma(-t * gi, w[i], bb);
                     }
                     const P q = cc - D2;
                     const P tau = (-bb + nls_sqrt(bb * bb - aa * q)) / aa;
 #pragma unroll
-                    for (int i = 0; i < N; ++i) d[i] = double(fma(tau, w[i], -t * g[i]));
+                    for (int i = 0; i < N; ++i) d[i] = double(fma(tau, w[i], -t * g(i)));
                     // J d = -s1 J g - tau F with s1 = (1 - tau) t
                     const P s1 = (P(1) - tau) * t;
                     pred = double(s1 * (P(2) * (P(1) - tau) * gg - s1 * JgJg) + tau * (P(2) - tau) * P(fF));
@@ -424,14 +467,6 @@ struct ThreadSolver {
         else if (it >= a.maxiters) status = ST_MAXITERS;
     }
 };
-
-constexpr int THREAD_TPB = 32; // one warp per CTA: lanes never wait on each other
-
-template <int N, int FAM, bool MIXED>
-constexpr int thread_smem_bytes()
-{
-    return THREAD_TPB * family_params<FAM>(N) * (8 + (MIXED ? 4 : 0));
-}
 
 // The lane loop shared by every one-instance-per-thread solver S (S::E
 // parameters, init / pass / finish, a status): each lane owns an instance

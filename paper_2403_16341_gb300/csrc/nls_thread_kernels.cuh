@@ -10,7 +10,7 @@ template <int N, int FAM, bool MIXED, bool ANALYTIC>
 cudaError_t launch_thread(const SolveArgs &a, int grid, cudaStream_t st)
 {
     k_solve_thread<N, FAM, MIXED, ANALYTIC>
-        <<<grid, THREAD_TPB, thread_smem_bytes<N, FAM, MIXED>(), st>>>(a);
+        <<<grid, THREAD_TPB, thread_newton_smem_bytes<N, FAM, MIXED>(), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -21,7 +21,7 @@ KernelInfo thread_info()
     k.launch = &launch_thread<N, FAM, MIXED, ANALYTIC>;
     k.func = reinterpret_cast<const void *>(&k_solve_thread<N, FAM, MIXED, ANALYTIC>);
     k.block = THREAD_TPB;
-    k.smem = thread_smem_bytes<N, FAM, MIXED>();
+    k.smem = thread_newton_smem_bytes<N, FAM, MIXED>();
     k.per_cta = THREAD_TPB;
     return k;
 }
