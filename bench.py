@@ -688,8 +688,15 @@ def config4_bratu_large(torch, solver, dev, stream, steps, warmup):
                           ("fp64_lu", TR)):
             ms, sv, nl = time_flush(torch, solver, dbs, alg, steps, max(warmup, 3), stream)
             passes = sum(int(outs[1].sum().item()) for *_, outs in dbs) / sum(b.batch for b, *_ in dbs)
+            # algorithmic flops of the factorisations and triangular solves of the
+            # passes (2n^3/3 - n^2/2 - n/6 + 2n^2 each; a refined pass adds two
+            # more solves of 2n^2), in the LU's precision
+            nsolve = 3 if alg & REFINE else 1
+            gf = sum(float(outs[1].sum().item()) * (2 * b.n ** 3 / 3 - b.n ** 2 / 2 - b.n / 6 + nsolve * 2 * b.n ** 2)
+                     for b, *_, outs in dbs) / 1e9
             res[name] = {"ms": ms, "solved_per_s": sv / (ms / 1e3), "solved": sv, "launches": nl,
-                         "mean_passes": passes}
+                         "mean_passes": passes, "lu_gflop": gf, "lu_tflops": gf / ms,
+                         "lu_precision": "fp32" if alg & MIXED else "fp64"}
             res[name]["max_rel_err"] = sampled_error(dbs, alg, 1)
     res["clocks"] = clk.summary()
     return res
