@@ -182,8 +182,10 @@ int nls_batch_create(nls_handle *out, int device, void *cuda_stream, size_t mem_
  * hardware interleaves.  *req receives an id for nls_status.
  * batch == 0 is a no-op that still returns an id.
  * Errors: NLS_E_INVALID (null pointers, negative batch/maxiters, bad abstol,
- * unknown algorithm), NLS_E_UNSUPPORTED (n outside [1, 128], unknown family,
- * tiling that cannot hold n). */
+ * unknown algorithm or flag), NLS_E_UNSUPPORTED (n outside [1, 128], unknown
+ * family, tiling that cannot hold n, a flag the algorithm does not take:
+ * NLS_ANALYTIC_JAC with NLS_POTRA_PTAK..NLS_MOD_BROYDEN, NLS_REFINE outside
+ * NLS_MIXED Newton / backtracking / trust region on the CTA tiling). */
 int nls_solve(nls_handle h, int family, const double *params, double *u, int n, int64_t batch,
               int alg, double abstol, int maxiters, const nls_outputs *out, int64_t *req);
 
