@@ -182,6 +182,27 @@ def test_host_entry_point_matches_device(solver, case):
     np.testing.assert_array_equal(nf, g["nfev"])
 
 
+def test_host_request_full_size_eight_chunks(solver):
+    # the end-to-end path of the benchmark: 2^20 instances on pinned host
+    # buffers, eight chunks whose solves alternate between two streams;
+    # every output equals the device-buffer path, bit for bit
+    import torch
+    import paper_2403_16341_gb300 as nls
+    b = I.cubic_batch(8, 1 << 20, config_id=1, b_half_width=5.0)
+    for alg in (TR, LS | MIXED):
+        ref = gpu_solve(solver, b, alg)
+        hp = torch.from_numpy(np.ascontiguousarray(b.params)).pin_memory()
+        hu = torch.from_numpy(np.ascontiguousarray(b.u0)).pin_memory()
+        hst = torch.zeros(b.batch, dtype=torch.int32).pin_memory()
+        hit = torch.zeros(b.batch, dtype=torch.int32).pin_memory()
+        req = nls.nls_solve_host_async(solver.h, b.family, hp.data_ptr(), hu.data_ptr(), b.n, b.batch, alg,
+                                       1e-10, 50, hst.data_ptr(), hit.data_ptr())
+        assert nls.nls_status(solver.h, req) == ref["solved"] == b.batch
+        np.testing.assert_array_equal(hu.numpy(), ref["u"])
+        np.testing.assert_array_equal(hst.numpy(), ref["status"])
+        np.testing.assert_array_equal(hit.numpy(), ref["iters"])
+
+
 def test_pending_device_request_then_chunked_host_request(solver):
     # a device-buffer request made with nls_solve and not yet flushed is
     # launched on the handle's stream before a host request's chunks, which
