@@ -36,6 +36,12 @@
 // column; in FP64, where each step's FMAs must be spread over the SM's few
 // FP64 units, the block-cyclic tiling (nls_cta.cuh) is kept.
 //
+// The factors stay in the warps' registers after the solve, so a second
+// right-hand side (lu_apply: the forward elimination replayed panel by panel,
+// then the back substitution) refines the Newton step when the request asks
+// for it: r = -F - J dN with J in FP64, evaluated row by row from the family,
+// and dN += the FP32 solve of r (classical iterative refinement).
+//
 // The Jacobian comes from forward-mode duals over the stencil of each row
 // (Sec. 2.4), the globalisations are those of the other tilings (Sec. 2.2).
 #pragma once
