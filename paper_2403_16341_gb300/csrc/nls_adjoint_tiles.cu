@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(CTA_TPB) k_adjoint_cta(AdjointTileArgs g)
             for (int bb = 0; bb < R; ++bb) a[aa][bb] = sm.U[s.col(bb)][s.row(aa)];
         if (s.tid < n) sm.rhs[s.tid] = g.w[(int64_t)s.tid * B + k];
         __syncthreads();
-        const bool ok = s.template lu_solve<false>(a, sm); // mu = J^-T w in sm.x (one factorisation: no compaction)
+        const bool ok = s.lu_solve(a, sm); // mu = J^-T w in sm.x
         if constexpr (FAM == FAM_CUBIC) {
             for (int idx = s.tid; idx < n * n; idx += CTA_TPB) {
                 const int i = idx / n, j = idx - i * n;
