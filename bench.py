@@ -675,6 +675,12 @@ def config2_uneven(torch, nls, local, dev, stream, steps, warmup, modes=True):
     return res
 
 
+def lu_pass_flops(n: int, solves: int = 1) -> float:
+    """Flops of one dense LU with partial pivoting (2n^3/3 - n^2/2 - n/6)
+    plus `solves` pairs of triangular solves (2n^2 each)."""
+    return 2 * n ** 3 / 3 - n ** 2 / 2 - n / 6 + solves * 2 * n ** 2
+
+
 def config4_bratu_large(torch, solver, dev, stream, steps, warmup):
     """16,384 Bratu instances, n uniform in 64..128, trust-region dogleg, one
     CTA per instance: the FP32 LU with FP64 residual (Newton's own correction
@@ -689,11 +695,9 @@ def config4_bratu_large(torch, solver, dev, stream, steps, warmup):
             ms, sv, nl = time_flush(torch, solver, dbs, alg, steps, max(warmup, 3), stream)
             passes = sum(int(outs[1].sum().item()) for *_, outs in dbs) / sum(b.batch for b, *_ in dbs)
             # algorithmic flops of the factorisations and triangular solves of the
-            # passes (2n^3/3 - n^2/2 - n/6 + 2n^2 each; a refined pass adds two
-            # more solves of 2n^2), in the LU's precision
+            # passes, in the LU's precision (a refined pass adds two more solves)
             nsolve = 3 if alg & REFINE else 1
-            gf = sum(float(outs[1].sum().item()) * (2 * b.n ** 3 / 3 - b.n ** 2 / 2 - b.n / 6 + nsolve * 2 * b.n ** 2)
-                     for b, *_, outs in dbs) / 1e9
+            gf = sum(float(outs[1].sum().item()) * lu_pass_flops(b.n, nsolve) for b, *_, outs in dbs) / 1e9
             res[name] = {"ms": ms, "solved_per_s": sv / (ms / 1e3), "solved": sv, "launches": nl,
                          "mean_passes": passes, "lu_gflop": gf, "lu_tflops": gf / ms,
                          "lu_precision": "fp32" if alg & MIXED else "fp64"}

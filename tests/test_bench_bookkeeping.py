@@ -62,3 +62,11 @@ def test_traffic_is_tied_to_the_kernel_sources(bench, monkeypatch):
     monkeypatch.setattr(bench, "THREAD_KERNEL_SOURCES", bench.THREAD_KERNEL_SOURCES[:-1])
     assert bench.thread_kernel_hash() != h
     assert all(bench.dram_traffic(v) is None for v in rows)
+
+
+def test_lu_pass_flops(bench):
+    # n = 8: 2n^3/3 - n^2/2 - n/6 = 308 and 2n^2 = 128 per solve pair; n = 128:
+    # 1,398,101.3 - 8,192 - 21.3 = 1,389,888 plus 32,768 per solve pair
+    assert bench.lu_pass_flops(8) == pytest.approx(308 + 128)
+    assert bench.lu_pass_flops(8, 3) == pytest.approx(308 + 3 * 128)
+    assert bench.lu_pass_flops(128) == pytest.approx(1389888 + 32768)
